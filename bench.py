@@ -1,0 +1,412 @@
+"""All-mode sparse MTTKRP benchmark (one JSON line on rank 0).
+
+Workload (default): the 3-mode skewed tensor 2^22 x 2^21 x 2^11 with 150M
+distinct nonzeros, Zipf(1.2) indices with permuted labels, U(0,1) values,
+rank 32, N(0,1) float32 factors -- synthetic, seeded, generated on the GPU.
+A step is one all-mode MTTKRP (modes 0, 1, 2) over the BLCO store with
+device-resident inputs; ``value`` is nonzeros processed per second per
+all-mode step, summed over ranks. The store and factors (about 2.6 GB) are
+larger than L2, so no flush is needed between steps.
+
+Also reported: ``e2e`` (the same step through the C ABI with pinned host
+factor matrices and host results, copies inside the timed region), the
+bfloat16-factor variant, the roofline of the MTTKRP kernel (algorithmic bytes
+per launch over its CUDA-event duration), the CPU baseline (the FP64 oracle
+on a bounded sample), and SM clocks sampled during the timed region.
+
+``--impl reference`` times the FP64 CPU oracle instead (rank 0 only).
+Multi-GPU: independent replicas, one per rank (no collective on the data
+path); the max time over ranks is used.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+from paper_2201_12523_gb300 import synth  # noqa: E402
+
+WORKLOADS = {s.name: s for s in synth.CONFIGS}
+DEFAULT_WORKLOAD = "zipf1.2-3d-150M"
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+
+# DRAM traffic of the MTTKRP kernel from an ncu capture (profiles/), valid only
+# for the kernel source it was taken from (sha256 of csrc/mttkrp.cu).
+TRAFFIC_RECORD = {"mttkrp_src_sha256": None, "bytes_per_launch": None}
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=30)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="blco", choices=["blco", "reference"])
+    p.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-bf16", action="store_true")
+    return p.parse_args(argv)
+
+
+# ----------------------------------------------------------------- ranks
+class Ranks:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+            if backend == "nccl":
+                torch.cuda.set_device(self.local)
+            dist.init_process_group(backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg is not None:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if self.pg is None:
+            return float(x)
+        dev = torch.device("cuda", self.local) if torch.cuda.is_available() else torch.device("cpu")
+        t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, x: float) -> float:
+        if self.pg is None:
+            return float(x)
+        dev = torch.device("cuda", self.local) if torch.cuda.is_available() else torch.device("cpu")
+        t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg is not None:
+            self.pg.destroy_process_group()
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- helpers
+def hbm_peak():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def mttkrp_src_sha() -> str:
+    with open(os.path.join(ROOT, "paper_2201_12523_gb300", "csrc", "mttkrp.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def algorithmic_bytes(spec, R: int, fbytes: int, mode: int) -> int:
+    """Compulsory bytes of one mode-n MTTKRP launch: the key/value stream
+    (8 + 4 bytes per nonzero), every other factor matrix once, the output once."""
+    b = 12 * spec.nnz + 4 * spec.dims[mode] * R
+    for k, d in enumerate(spec.dims):
+        if k != mode:
+            b += d * R * fbytes
+    return b
+
+
+def gen_inputs(spec, device):
+    coords = synth.coordinates(spec, device=device)
+    vals = synth.values(spec, device=device)
+    A = synth.factors(spec, device=device)
+    return coords, vals, A
+
+
+# ----------------------------------------------------------------- CPU arms
+def cpu_oracle_rate(spec, coords, vals, A, sample_nnz: int, repeats: int = 1):
+    """The FP64 oracle, as it stands, on the first `sample_nnz` nonzeros of the
+    workload (a random subset: the COO is in random order), all modes.
+    Returns (nnz/s, seconds per step)."""
+    import oracle
+
+    oracle.build()
+    c = coords[:sample_nnz].cpu().numpy().astype(np.uint32)
+    v = vals[:sample_nnz].cpu().numpy().astype(np.float64)
+    Af = [a.cpu().numpy().astype(np.float64) for a in A]
+    times = []
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        for n in range(spec.order):
+            oracle.mttkrp(c, v, spec.dims, Af, n)
+        times.append(time.perf_counter() - t0)
+    sec = statistics.median(times)
+    return sample_nnz / sec, sec
+
+
+def run_reference(args, ranks: Ranks):
+    if ranks.rank != 0:
+        return 0
+    spec = WORKLOADS[args.workload]
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    coords, vals, A = gen_inputs(spec, dev)
+    sample = min(spec.nnz, 400_000)
+    import oracle
+
+    oracle.build()
+    c = coords[:sample].cpu().numpy().astype(np.uint32)
+    v = vals[:sample].cpu().numpy().astype(np.float64)
+    Af = [a.cpu().numpy().astype(np.float64) for a in A]
+    del coords, vals, A
+
+    def step():
+        for n in range(spec.order):
+            oracle.mttkrp(c, v, spec.dims, Af, n)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    sec = (time.perf_counter() - t0) / max(args.steps, 1)
+    value = sample / sec
+    sample_desc = (f"first {sample} of the workload's {spec.nnz} nonzeros (random order), all "
+                   f"{spec.order} modes per step, FP64, single thread")
+    line = {"impl": "reference", "metric": "all-mode sparse MTTKRP throughput", "value": value,
+            "unit": "nnz/s (all-mode)", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "config": {"workload": spec.name, "rank": spec.rank},
+            "cpu_baseline": {"value": value, "unit": "nnz/s (all-mode)", "cores": 1, "kind": "oracle",
+                             "sample": sample_desc},
+            "e2e": {"value": value, "unit": "nnz/s (all-mode)", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------- GPU arm
+def time_steps(step, K: int, stream) -> float:
+    """ms for K steps, CUDA events on the launching stream."""
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(K):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def run_blco(args, ranks: Ranks):
+    from paper_2201_12523_gb300 import blco
+
+    dev = torch.device("cuda", ranks.local)
+    torch.cuda.set_device(dev)
+    spec = WORKLOADS[args.workload]
+    R = spec.rank
+    t_gen = time.perf_counter()
+    coords, vals, A = gen_inputs(spec, dev)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t_gen
+
+    stream = torch.cuda.current_stream()
+    eb0, eb1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    eb0.record(stream)
+    t = blco.Tensor.build(coords, vals, spec.dims)
+    eb1.record(stream)
+    torch.cuda.synchronize()
+    build_ms = eb0.elapsed_time(eb1)
+    info = t.info()
+
+    outs = [torch.empty((d, R), dtype=torch.float32, device=dev) for d in spec.dims]
+
+    def make_step(factors):
+        def step():
+            for n in range(spec.order):
+                t.mttkrp(n, factors, out=outs[n])
+        return step
+
+    step32 = make_step(A)
+    for _ in range(args.warmup):
+        step32()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(ranks.local)
+    sampler.start()
+    ranks.barrier()
+    blco.blco_profile_enable(t.handle, True)
+    ms = time_steps(step32, args.steps, stream)
+    blco.blco_profile_enable(t.handle, False)
+    prof = blco.blco_profile_read(t.handle)
+    ranks.barrier()
+    clocks = sampler.stop()
+    ms_max = ranks.max(ms)
+    ms_per_step = ms_max / args.steps
+    total_nnz = ranks.sum(spec.nnz * args.steps)
+    value = total_nnz / (ms_max / 1e3)
+
+    # roofline of the MTTKRP kernel: algorithmic bytes / mean launch duration
+    peak, peak_src = hbm_peak()
+    launches, kms = prof.get("mttkrp", (0, 0.0))
+    zl, zms = prof.get("zero", (0, 0.0))
+    bytes_all = sum(algorithmic_bytes(spec, R, 4, n) for n in range(spec.order))
+    per_launch_bytes = bytes_all / spec.order
+    per_launch_ms = kms / max(launches, 1)
+    achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9 if launches else None
+    traffic = None
+    if TRAFFIC_RECORD["mttkrp_src_sha256"] == mttkrp_src_sha():
+        traffic = TRAFFIC_RECORD["bytes_per_launch"]
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                "kernel": "k_mttkrp<float,32>", "peak_source": peak_src + " (burst copy, MEASURED_PEAKS hbm_gbs)",
+                "algorithmic_bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_ms}
+
+    extra = {}
+    # bfloat16 factors, same step
+    if not args.no_bf16:
+        A16 = [blco.convert(a, torch.bfloat16) for a in A]
+        step16 = make_step(A16)
+        for _ in range(args.warmup):
+            step16()
+        blco.blco_profile_enable(t.handle, True)
+        ms16 = ranks.max(time_steps(step16, args.steps, stream))
+        blco.blco_profile_enable(t.handle, False)
+        p16 = blco.blco_profile_read(t.handle)
+        l16, k16 = p16.get("mttkrp", (0, 0.0))
+        b16 = sum(algorithmic_bytes(spec, R, 2, n) for n in range(spec.order)) / spec.order
+        ach16 = b16 / (k16 / max(l16, 1) / 1e3) / 1e9 if l16 else None
+        extra["bf16"] = {"value": total_nnz / (ms16 / 1e3), "ms_per_step": ms16 / args.steps,
+                         "speedup_vs_f32": ms_max / ms16, "roofline_frac": (ach16 / peak) if ach16 else None,
+                         "error_bound": 1e-2, "error_vs": "FP64 oracle on the unrounded float32 factors"}
+        del A16
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        Ah = [a.cpu().pin_memory() for a in A]
+        Oh = [torch.empty((d, R), dtype=torch.float32).pin_memory() for d in spec.dims]
+        Ah_np = [a.numpy() for a in Ah]
+        Oh_np = [o.numpy() for o in Oh]
+
+        def step_e2e():
+            blco.blco_mttkrp_all(t.handle, Ah_np, blco.BLCO_F32, R, Oh_np, stream)
+
+        step_e2e()
+        K2 = max(1, min(args.steps, 10))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(K2):
+            step_e2e()
+        torch.cuda.synchronize()
+        sec = ranks.max((time.perf_counter() - t0) / K2)
+        h2d = sum(d * R * 4 for d in spec.dims)
+        d2h = h2d
+        e2e = {"value": ranks.sum(spec.nnz) / sec, "unit": "nnz/s (all-mode)", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": sec * 1e3, "steps": K2,
+               "note": "blco_mttkrp_all with pinned host factors and host results; store resident"}
+
+    cpu = None
+    if not args.no_cpu and ranks.rank == 0:
+        sample = min(spec.nnz, 1_000_000)
+        rate, sec = cpu_oracle_rate(spec, coords, vals, A, sample)
+        cpu = {"value": rate, "unit": "nnz/s (all-mode)", "cores": 1, "kind": "oracle",
+               "sample": f"first {sample} nonzeros of the workload (random order), all {spec.order} modes, "
+                         f"FP64 C loops, one thread, {sec:.2f} s"}
+
+    line = {"metric": "all-mode sparse MTTKRP throughput", "value": value, "unit": "nnz/s (all-mode)",
+            "n_gpus": ranks.world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": spec.name, "dims": list(spec.dims), "nnz": spec.nnz, "rank": R,
+                       "factors": "float32 N(0,1)", "values": "U(0,1)", "index_dist": "Zipf(1.2), permuted labels",
+                       "parallelism": f"replicas x{ranks.world}",
+                       "l2": "inputs larger than L2 (store 1.8 GB + factors 0.8 GB), no flush"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": int(launches + zl),
+            "build_ms": build_ms, "gen_s": gen_s, "store": {"nblocks": info["nblocks"], "hot_rows": info["hot_rows"],
+                                                          "device_bytes": info["device_bytes"]}}
+    line.update(extra)
+    if ranks.rank == 0:
+        print(json.dumps(line), flush=True)
+    t.destroy()
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    ranks = Ranks()
+    try:
+        if args.impl == "reference":
+            return run_reference(args, ranks)
+        return run_blco(args, ranks)
+    finally:
+        ranks.close()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,253 @@
+/*
+ * blco.h -- C ABI of libblco.so: sparse MTTKRP over a blocked, linearized
+ * coordinate (BLCO) store on one NVIDIA GB300 (sm_103a).
+ *
+ * The paper ("Efficient, Out-of-Memory Sparse MTTKRP on Massively Parallel
+ * Architectures", ICS'22) states the problem this library solves:
+ *   - Eq. 1 (Section 2.3): the mode-n MTTKRP of an N-mode sparse tensor X
+ *     with factor matrices A_1..A_N is M = X_(n) (A_N (.) ... (.) A_{n+1}
+ *     (.) A_{n-1} (.) ... (.) A_1), computed per nonzero as in Fig. 3:
+ *     M[i_n, :] += x * (Hadamard product of rows A_k[i_k, :], k != n).
+ *   - Section 4: the BLCO store -- each nonzero's N indices linearized in
+ *     ALTO order (Section 4.1, Fig. 6a), re-encoded as concatenated per-mode
+ *     bit fields so that de-linearization is shift and mask (Fig. 6b), the
+ *     bits above a 64-bit encoding line kept once per block (Section 4.2),
+ *     blocks split at a nonzero cap and streamed from host memory when the
+ *     tensor exceeds the device (Section 4.2, device queues).
+ *   - Algorithm 1 (Section 2.2): CP-ALS, whose per-mode update needs the
+ *     MTTKRP and the Hadamard product of the other factors' Grams.
+ *
+ * Conventions for every call:
+ *   - Indices are 0-based (the paper's figures are 1-based).
+ *   - Matrices are row-major: a factor A_k is I_k x R with the rank index
+ *     contiguous; an MTTKRP result is I_n x R float32.
+ *   - "Store order" is the order of nonzeros inside the store: blocks by
+ *     block key, ALTO order inside a block, input order among duplicates.
+ *   - Pointers marked "host or device" are classified with
+ *     cudaPointerGetAttributes: device and managed memory are used in place;
+ *     host memory (pinned or pageable) is copied through library-owned device
+ *     buffers inside the call.
+ *   - Calls are stream-ordered on the given stream (NULL = the legacy
+ *     default stream) and return before the GPU work completes, except where
+ *     a host pointer is involved, in which case the call synchronizes the
+ *     stream before returning so that host results are complete.
+ *   - Argument errors return at once with no work enqueued. Errors of
+ *     enqueued GPU work surface as BLCO_ERR_CUDA on a later call or on
+ *     blco_sync. blco_last_error() gives a message for the calling thread.
+ *   - The caller owns every pointer it passes; the handle owns the store,
+ *     its block table, queue buffers and workspace, all freed by
+ *     blco_destroy. A handle may be used by one thread at a time.
+ */
+#ifndef BLCO_H
+#define BLCO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BLCO_MAX_MODES 8
+
+typedef struct blco_tensor *blco_handle;
+/* A cudaStream_t (both are pointers to struct CUstream_st). */
+typedef struct CUstream_st *blco_stream;
+
+typedef enum {
+    BLCO_OK = 0,
+    BLCO_ERR_ARG = 1,         /* bad argument: null pointer, size, mode, rank, dtype */
+    BLCO_ERR_INDEX = 2,       /* a coordinate is outside its mode's length */
+    BLCO_ERR_OOM = 3,         /* device/host allocation failed or budget exceeded */
+    BLCO_ERR_CUDA = 4,        /* a CUDA runtime call or kernel failed */
+    BLCO_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+    BLCO_ERR_STATE = 6,       /* handle in the wrong state for the call */
+    BLCO_ERR_UNSUPPORTED = 7  /* valid request this build does not implement */
+} blco_status;
+
+typedef enum { BLCO_F32 = 0, BLCO_BF16 = 1, BLCO_F16 = 2 } blco_dtype;
+
+/* Construction options (Section 4.2). Zero-initialized fields take defaults. */
+typedef struct {
+    int64_t max_nnz_per_block;   /* block cap; 0 = 2^27 (the paper's setting) */
+    int32_t line_bits;           /* encoding line length, 1..64; 0 = 64 */
+    int32_t n_queues;            /* streaming device queues, 1..8; 0 = 8 */
+    int64_t device_budget_bytes; /* cap on this handle's device memory; 0 = none */
+    int32_t force_stream;        /* 1 = keep the store in pinned host memory */
+    int32_t reserved;
+} blco_build_opts;
+
+typedef struct {
+    int64_t nnz;
+    int32_t order;                         /* N */
+    int32_t total_bits;                    /* B = sum_n ceil(log2 I_n) */
+    int64_t dims[BLCO_MAX_MODES];
+    int32_t mode_bits[BLCO_MAX_MODES];     /* b_n */
+    int32_t block_bits[BLCO_MAX_MODES];    /* bits of mode n above the line */
+    int32_t line_bits;
+    int32_t streamed;                      /* 1 if the store lives in pinned host memory */
+    int64_t nblocks;
+    int64_t max_nnz_per_block;
+    int64_t queue_nnz;                     /* per-queue reservation (streamed stores) */
+    int32_t n_queues;
+    int32_t hot_rows[BLCO_MAX_MODES];      /* rows per mode accumulated on chip */
+    int64_t device_bytes;                  /* device memory held by the handle */
+    int64_t host_bytes;                    /* pinned host memory held by the handle */
+} blco_info_t;
+
+/* Fills *opts with the defaults. Returns BLCO_ERR_ARG for a null pointer. */
+blco_status blco_default_opts(blco_build_opts *opts);
+
+/*
+ * Builds the BLCO store of a COO tensor (Section 4: linearize in ALTO order,
+ * stable sort, block by the bits above the line, split at the cap,
+ * re-encode). All steps run on the current CUDA device.
+ *   coords  nnz x N uint32, row-major, 0-based (host or device)
+ *   vals    nnz float32 (host or device)
+ *   dims    N mode lengths I_n >= 1 (host), N in 1..BLCO_MAX_MODES,
+ *           sum of ceil(log2 I_n) <= 128, each I_n <= 2^32
+ *   opts    NULL for the defaults
+ *   stream  stream for the construction work; the call synchronizes it
+ *   out     receives the handle (NULL on error)
+ * Duplicate coordinates are kept as separate nonzeros (input order).
+ * Errors: BLCO_ERR_ARG, BLCO_ERR_INDEX (a coordinate >= its I_n),
+ * BLCO_ERR_OOM, BLCO_ERR_CUDA. nnz may be 0.
+ */
+blco_status blco_build(const uint32_t *coords, const float *vals, int64_t nnz, const int64_t *dims,
+                       int N, const blco_build_opts *opts, blco_stream stream, blco_handle *out);
+
+/*
+ * Mode-`mode` MTTKRP (Eq. 1, Fig. 3) of the stored tensor:
+ *   out[i, r] = sum over nonzeros with i_mode = i of x * prod_{k != mode} A_k[i_k, r].
+ *   factors  N pointers (host or device); factors[k] is I_k x R of type fdt;
+ *            factors[mode] is not read and may be NULL
+ *   R        rank: 8, 16, 32, 64 or 128
+ *   out      I_mode x R float32 (host or device); overwritten
+ * Accumulation is float32 (segmented within a warp, then on-chip per CTA for
+ * the handle's hot rows, then vector reductions to global memory), so the
+ * summation order, and the last bits, vary from run to run.
+ * Errors: BLCO_ERR_ARG, BLCO_ERR_UNSUPPORTED (rank), BLCO_ERR_OOM (staging),
+ * BLCO_ERR_CUDA.
+ */
+blco_status blco_mttkrp(blco_handle h, int mode, const void *const *factors, blco_dtype fdt, int R,
+                        float *out, blco_stream stream);
+
+/*
+ * All-mode MTTKRP with one set of factors: outs[n] = mode-n MTTKRP for every
+ * n with outs[n] != NULL (Eq. 1 for each mode, as the paper's all-mode
+ * measurements do). Same arguments and errors as blco_mttkrp; host factor
+ * matrices are staged to the device once for all modes.
+ */
+blco_status blco_mttkrp_all(blco_handle h, const void *const *factors, blco_dtype fdt, int R,
+                            float *const *outs, blco_stream stream);
+
+/*
+ * CP model at every stored nonzero (Algorithm 1's model, Section 2.2):
+ *   xhat[j] = sum_r prod_n A_n[i_n^j, r], j in store order.
+ *   factors  N matrices I_n x R (host or device); xhat: nnz float32 (host or device)
+ */
+blco_status blco_cp_fwd(blco_handle h, const void *const *factors, blco_dtype fdt, int R,
+                        float *xhat, blco_stream stream);
+
+/*
+ * Adjoint of blco_cp_fwd for mode `mode`: given g = dL/dxhat (nnz float32,
+ * store order, host or device), out = dL/dA_mode = mode-`mode` MTTKRP with g
+ * in place of the tensor values (Eq. 1); row products are recomputed, not
+ * stored. out: I_mode x R float32 (host or device), overwritten.
+ */
+blco_status blco_cp_bwd(blco_handle h, int mode, const float *grad, const void *const *factors,
+                        blco_dtype fdt, int R, float *out, blco_stream stream);
+
+/* Copies out the store: values (nnz float32), input positions (nnz int64:
+ * store position -> input row), in-block keys (nnz uint64). Host or device
+ * destinations. */
+blco_status blco_values(blco_handle h, float *vals, blco_stream stream);
+blco_status blco_perm(blco_handle h, int64_t *perm, blco_stream stream);
+blco_status blco_keys(blco_handle h, uint64_t *keys, blco_stream stream);
+
+/* Block table (host arrays): bstart[nblocks + 1] store offsets and
+ * bhigh[nblocks * N] the per-mode index bits above each mode's in-block
+ * field (i_n = (bhigh[b*N+n] << field_width_n) | field_n). */
+blco_status blco_blocks(blco_handle h, int64_t *bstart, uint32_t *bhigh);
+
+/* Shape, layout and memory of the handle. */
+blco_status blco_info(blco_handle h, blco_info_t *info);
+
+/* Waits for all of the handle's work; reports asynchronous GPU errors. */
+blco_status blco_sync(blco_handle h);
+
+/* Frees everything the handle owns (waits for its work first). NULL is a no-op. */
+void blco_destroy(blco_handle h);
+
+/* Message for the last failed call on the calling thread ("" if none). */
+const char *blco_last_error(void);
+
+/*
+ * float32 -> bfloat16 / float16 conversion, round to nearest even (for
+ * factor matrices stored at 16 bits). src: n float32 (device), dst: n 16-bit
+ * values (device). dt must be BLCO_BF16 or BLCO_F16.
+ */
+blco_status blco_convert(const float *src, void *dst, blco_dtype dt, int64_t n, blco_stream stream);
+
+/*
+ * FP64 pieces of CP-ALS (Algorithm 1), on the device.
+ *
+ * blco_gram: G = A^T A (R x R float64, device), A is I x R of type fdt
+ * (device). Products of two float32 (or 16-bit) entries are exact in
+ * float64; the sum runs in float64.
+ */
+blco_status blco_gram(const void *A, blco_dtype fdt, int64_t I, int R, double *G, blco_stream stream);
+
+/*
+ * blco_cpals_update: the factor update of Algorithm 1 for one mode.
+ *   grams   N device pointers to the R x R float64 Grams; grams[mode] unused
+ *   M       I x R float32 MTTKRP of `mode` (device)
+ *   A       I x R float32 output (device): A = M V^+ with V the Hadamard
+ *           product of the other Grams, columns scaled to unit 2-norm
+ *   lambda  R float64 output (device): the column norms removed from A
+ *   G_out   R x R float64 output (device): Gram of the new A (may be NULL)
+ *   info    1 int32 (device): 0 if V was positive definite (Cholesky),
+ *           1 if the eigen pseudo-inverse was used
+ * R <= 128.
+ */
+blco_status blco_cpals_update(const double *const *grams, int N, int mode, int R, const float *M,
+                              int64_t I, float *A, double *lambda, double *G_out, int32_t *info,
+                              blco_stream stream);
+
+/*
+ * blco_cpals_fit: fit = 1 - ||X - Xhat|| / ||X|| of the model (lambda, A_1..A_N)
+ * from ||X||^2 (host value), all N Grams, lambda, and the last mode's M and A:
+ *   ||Xhat||^2 = lambda^T (Hadamard product of all Grams) lambda
+ *   <X, Xhat>  = sum_r lambda_r sum_i M[i, r] A_last[i, r]
+ * fit: 1 float64 (device).
+ */
+blco_status blco_cpals_fit(double normX2, const double *const *grams, int N, int R,
+                           const double *lambda, const float *M_last, const float *A_last,
+                           int64_t I_last, double *fit, blco_stream stream);
+
+/* sum_j vals[j]^2 in float64 over the stored values (device result). */
+blco_status blco_norm2(blco_handle h, double *out, blco_stream stream);
+
+/*
+ * Kernel timing (measurement support; no counterpart in the paper). While
+ * enabled, the handle records a CUDA event pair on the launching stream
+ * around each kernel it launches. blco_profile_read waits for the recorded
+ * events and returns one entry per kernel kind ("zero", "mttkrp", "cp_fwd",
+ * "norm2") with the number of launches and their summed duration, then
+ * clears the record. count receives the number of entries written (at most
+ * capacity). Enabling costs two event records per launch.
+ */
+typedef struct {
+    char name[32];
+    int64_t launches;
+    double total_ms;
+} blco_profile_entry;
+
+blco_status blco_profile_enable(blco_handle h, int enable);
+blco_status blco_profile_read(blco_handle h, blco_profile_entry *entries, int capacity, int *count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BLCO_H */

@@ -52,10 +52,13 @@ class TensorSpec:
         return len(self.dims)
 
     def scaled(self, nnz: int, dims: Sequence[int], name: Optional[str] = None) -> "TensorSpec":
-        """Same recipe at a smaller size (for oracle-sized parity cases)."""
-        return dataclasses.replace(
-            self, name=name or f"{self.name}-small", nnz=int(nnz), dims=tuple(int(d) for d in dims)
-        )
+        """Same recipe at a smaller size (for oracle-sized parity cases). With
+        a different number of modes, every mode takes the first mode's index
+        distribution."""
+        dims = tuple(int(d) for d in dims)
+        dist = self.index_dist if len(dims) == len(self.index_dist) else (self.index_dist[0],) * len(dims)
+        return dataclasses.replace(self, name=name or f"{self.name}-small", nnz=int(nnz), dims=dims,
+                                   index_dist=dist)
 
 
 def _z(alpha: float, n: int) -> Tuple[str, ...]:

@@ -1,0 +1,316 @@
+"""GPU parity of the BLCO library against the FP64 oracle (oracle-sized
+cases: several tiles, ragged tails, blocked and streamed stores, every rank
+and factor type, edge cases). Everything goes through the C ABI."""
+
+import ctypes
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2201_12523_gb300 import synth
+from tests._util import BF16_TOL, CP_TOL, FP32_TOL, check_mttkrp_all, make, rounded16, to_np64
+
+pytestmark = pytest.mark.gpu
+
+blco = pytest.importorskip("paper_2201_12523_gb300.blco")
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "blco_worked_example.txt")
+
+
+def _store_equal(t, coords, vals, dims, line_bits, cap):
+    ref = oracle.build_store(coords.cpu().numpy(), vals.cpu().numpy(), dims, line_bits, cap)
+    keys = t.keys()
+    perm = t.perm()
+    svals = t.values().cpu().numpy()
+    bstart, bhigh = t.blocks()
+    assert np.array_equal(perm, ref.perm)
+    assert np.array_equal(keys, ref.keys)
+    assert np.array_equal(svals.view(np.uint32), ref.svals.view(np.uint32))
+    assert np.array_equal(bstart, ref.bstart)
+    assert np.array_equal(bhigh, ref.bhigh)
+
+
+# ------------------------------------------------------------ construction
+def test_worked_example_store_bit_exact():
+    rows = []
+    for line in open(GOLDEN):
+        t = line.split()
+        if t and not line.startswith("#") and t[0] != "store_order":
+            rows.append([int(t[0]) - 1, int(t[1]) - 1, int(t[2]) - 1, float(t[3])])
+    coords = torch.tensor([r[:3] for r in rows], dtype=torch.int32)
+    vals = torch.tensor([r[3] for r in rows], dtype=torch.float32)
+    t = blco.Tensor.build(coords.cuda(), vals.cuda(), (4, 4, 4), line_bits=5, max_nnz_per_block=6)
+    _store_equal(t, coords, vals, (4, 4, 4), 5, 6)
+    assert t.values().cpu().tolist() == [1.0, 2.0, 4.0, 8.0, 6.0, 9.0, 5.0, 3.0, 10.0, 11.0, 7.0, 12.0]
+
+
+@pytest.mark.parametrize("dims,nnz,line,cap", [
+    ((1000, 800, 600), 100_000, 64, 1 << 27),          # uniform 3-mode, one block
+    ((1 << 14, 1 << 13, 1 << 7), 54_321, 64, 5000),     # split at a small cap, ragged
+    ((1 << 12, 1 << 10, 1 << 8, 64, 16), 77_777, 30, 1 << 27),  # 40 index bits over a 30-bit line
+    ((1 << 24, 1 << 20, 1 << 16, 1 << 12, 1 << 8), 200_000, 64, 3000),  # 80 bits: 16 block bits
+    ((37, 5, 1, 3), 500, 4, 7),                         # a mode of length 1, tiny blocks
+    ((1 << 20,), 4097, 64, 1 << 27),                    # 1 mode
+])
+def test_store_bit_exact(dims, nnz, line, cap):
+    spec = synth.small(1, nnz, dims) if len(dims) != 5 else synth.small(3, nnz, dims)
+    coords = synth.coordinates(spec, device="cuda")
+    vals = synth.values(spec, device="cuda")
+    t = blco.Tensor.build(coords, vals, dims, line_bits=line, max_nnz_per_block=cap)
+    _store_equal(t, coords, vals, dims, line, cap)
+
+
+def test_store_from_host_arrays_and_duplicates():
+    rng = np.random.default_rng(0)
+    dims = (50, 40, 30)
+    c = rng.integers(0, 30, (3000, 3)).astype(np.uint32)  # many duplicates
+    v = rng.random(3000).astype(np.float32)
+    t = blco.Tensor.build(c, v, dims)
+    _store_equal(t, torch.from_numpy(c.astype(np.int32)), torch.from_numpy(v), dims, 64, 1 << 27)
+
+
+def test_empty_and_single():
+    t = blco.Tensor.build(torch.zeros((0, 3), dtype=torch.int32, device="cuda"),
+                          torch.zeros(0, device="cuda"), (5, 6, 7))
+    assert t.nnz == 0
+    A = [torch.randn(d, 16, device="cuda") for d in (5, 6, 7)]
+    for n in range(3):
+        assert torch.count_nonzero(t.mttkrp(n, A)) == 0
+    c = torch.tensor([[4, 5, 6]], dtype=torch.int32, device="cuda")
+    v = torch.tensor([2.0], device="cuda")
+    t1 = blco.Tensor.build(c, v, (5, 6, 7))
+    M = t1.mttkrp(0, A).cpu().numpy()
+    ref = 2.0 * A[1][5].cpu().numpy() * A[2][6].cpu().numpy()
+    np.testing.assert_allclose(M[4], ref, rtol=1e-6)
+    assert np.count_nonzero(M[:4]) == 0
+
+
+def test_out_of_range_coordinate_is_index_error():
+    c = torch.tensor([[0, 0, 0], [1, 6, 0], [2, 1, 1]], dtype=torch.int32, device="cuda")
+    v = torch.ones(3, device="cuda")
+    with pytest.raises(blco.BlcoError) as ei:
+        blco.Tensor.build(c, v, (5, 6, 7))
+    assert ei.value.status == blco.BLCO_ERR_INDEX
+
+
+# ------------------------------------------------------------ MTTKRP
+@pytest.mark.parametrize("R", [8, 16, 32, 64, 128])
+def test_mttkrp_uniform_all_ranks(R):
+    spec = synth.small(0, 30_011, (1000, 800, 600))
+    coords, vals, _ = make(spec)
+    A = synth.factors(spec, rank=R, device="cuda")
+    t = blco.Tensor.build(coords, vals, spec.dims)
+    check_mttkrp_all(t, coords, vals, A, spec.dims)
+
+
+def test_mttkrp_uniform_100k_full():
+    spec = synth.CONFIGS[0]
+    coords, vals, A = make(spec)
+    t = blco.Tensor.build(coords, vals, spec.dims)
+    check_mttkrp_all(t, coords, vals, A, spec.dims)
+
+
+@pytest.mark.parametrize("idx,nnz,dims", [
+    (1, 300_000, (1 << 16, 1 << 15, 1 << 11)),               # Zipf 1.2, 3 modes, one mode fits on chip
+    (2, 300_000, (1 << 14, 1 << 12, 1 << 10, 1 << 8)),        # Zipf 1.1, 4 modes, lognormal values
+    (3, 200_000, (1 << 24, 1 << 20, 1 << 16, 1 << 12, 1 << 8)),  # 5 modes, 80 bits -> blocks
+    (4, 200_000, (1 << 14, 1 << 14, 1 << 10)),                # planted-model shape, R=64
+])
+def test_mttkrp_skewed_f32(idx, nnz, dims):
+    spec = synth.small(idx, nnz, dims)
+    coords, vals, A = make(spec)
+    t = blco.Tensor.build(coords, vals, spec.dims)
+    check_mttkrp_all(t, coords, vals, A, spec.dims)
+
+
+def test_mttkrp_positive_heavy_rows():
+    """All terms positive on a Zipf head (the hardest case for float32 sums)."""
+    spec = synth.small(1, 400_000, (1 << 12, 1 << 11, 1 << 11))
+    coords, vals, _ = make(spec)
+    A = synth.factors(spec, device="cuda", dist="u01")
+    t = blco.Tensor.build(coords, vals, spec.dims)
+    check_mttkrp_all(t, coords, vals, A, spec.dims)
+
+
+@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])
+def test_mttkrp_16bit_factors(dtype):
+    spec = synth.small(2, 300_000, (1 << 14, 1 << 12, 1 << 10, 1 << 8))
+    coords, vals, A = make(spec)
+    A16 = [blco.convert(a, dtype) for a in A]
+    t = blco.Tensor.build(coords, vals, spec.dims)
+    # accumulation error alone: oracle on the rounded factors
+    check_mttkrp_all(t, coords, vals, A16, spec.dims, tol=FP32_TOL, factors_ref=rounded16(A, dtype))
+    # total error against the unrounded float32 factors
+    check_mttkrp_all(t, coords, vals, A16, spec.dims, tol=BF16_TOL, factors_ref=to_np64(A))
+
+
+def test_convert_matches_oracle_rounding():
+    x = torch.randn(100_003, device="cuda") * 3
+    y = blco.convert(x, torch.bfloat16)
+    ref = oracle.bf16_round(x.cpu().numpy())
+    assert np.array_equal(y.float().cpu().numpy().view(np.uint32), ref.view(np.uint32))
+
+
+@pytest.mark.parametrize("nq", [1, 3, 8])
+def test_streamed_store_matches(nq):
+    spec = synth.small(3, 150_000, (1 << 24, 1 << 20, 1 << 16, 1 << 12, 1 << 8))
+    coords, vals, A = make(spec)
+    t = blco.Tensor.build(coords, vals, spec.dims, force_stream=True, max_nnz_per_block=4000, n_queues=nq)
+    info = t.info()
+    assert info["streamed"] and info["nblocks"] > 30
+    check_mttkrp_all(t, coords, vals, A, spec.dims)
+    _store_equal(t, coords, vals, spec.dims, 64, 4000)
+
+
+def test_budget_forces_streaming():
+    spec = synth.small(1, 200_000, (1 << 16, 1 << 15, 1 << 11))
+    coords, vals, A = make(spec)
+    t = blco.Tensor.build(coords, vals, spec.dims, device_budget_bytes=2_000_000, max_nnz_per_block=20_000,
+                          n_queues=4)
+    info = t.info()
+    assert info["streamed"] and info["device_bytes"] <= 2_000_000
+    check_mttkrp_all(t, coords, vals, A, spec.dims)
+
+
+def test_host_factor_and_output_pointers():
+    spec = synth.small(1, 100_000, (1 << 14, 1 << 13, 1 << 9))
+    coords, vals, A = make(spec)
+    t = blco.Tensor.build(coords.cpu().numpy().astype(np.uint32), vals.cpu().numpy(), spec.dims)
+    Ah = [a.cpu().numpy() for a in A]
+    outs = [np.empty((d, spec.rank), np.float32) for d in spec.dims]
+    blco.blco_mttkrp_all(t.handle, Ah, blco.BLCO_F32, spec.rank, outs)
+    c = coords.cpu().numpy()
+    v = vals.cpu().numpy().astype(np.float64)
+    for n in range(3):
+        M, S = oracle.mttkrp(c, v, spec.dims, to_np64(A), n)
+        assert oracle.max_rel_err(outs[n], M, S) <= FP32_TOL
+
+
+def test_argument_errors():
+    spec = synth.small(0, 1000, (10, 20, 30))
+    coords, vals, A = make(spec)
+    t = blco.Tensor.build(coords, vals, spec.dims)
+    out = torch.empty((10, 16), device="cuda")
+    with pytest.raises(blco.BlcoError) as ei:
+        blco.blco_mttkrp(t.handle, 0, A, blco.BLCO_F32, 24, out)
+    assert ei.value.status == blco.BLCO_ERR_UNSUPPORTED
+    with pytest.raises(blco.BlcoError) as ei:
+        blco.blco_mttkrp(t.handle, 3, A, blco.BLCO_F32, 16, out)
+    assert ei.value.status == blco.BLCO_ERR_ARG
+    bad = torch.empty(10 * 16 + 1, device="cuda")[1:].view(10, 16)
+    with pytest.raises(blco.BlcoError) as ei:
+        blco.blco_mttkrp(t.handle, 0, A, blco.BLCO_F32, 16, bad)
+    assert ei.value.status == blco.BLCO_ERR_ARG
+
+
+# ------------------------------------------------------------ CP model
+def _cp_ref(t, coords, A):
+    c = coords.cpu().numpy()[t.perm()]
+    Af = to_np64(A)
+    return oracle.cp_model(c, Af), oracle.cp_model(c, [np.abs(a) for a in Af])
+
+
+@pytest.mark.parametrize("R", [16, 64])
+def test_cp_fwd_matches(R):
+    spec = synth.small(4, 150_000, (1 << 14, 1 << 14, 1 << 10))
+    coords, vals, _ = make(spec)
+    A = synth.factors(spec, rank=R, device="cuda", dist="normal")
+    t = blco.Tensor.build(coords, vals, spec.dims)
+    xhat = t.cp_fwd(A).cpu().numpy()
+    ref, scale = _cp_ref(t, coords, A)
+    assert float(np.max(np.abs(xhat - ref) / scale)) <= CP_TOL
+
+
+def test_cp_bwd_is_mttkrp_with_gradient_values():
+    spec = synth.small(4, 150_000, (1 << 14, 1 << 14, 1 << 10))
+    coords, vals, A = make(spec)
+    t = blco.Tensor.build(coords, vals, spec.dims)
+    g = torch.randn(spec.nnz, device="cuda")
+    c = coords.cpu().numpy()[t.perm()]
+    gn = g.cpu().numpy().astype(np.float64)
+    for n in range(3):
+        out = t.cp_bwd(n, g, A).cpu().numpy()
+        M, S = oracle.mttkrp(c, gn, spec.dims, to_np64(A), n)
+        assert oracle.max_rel_err(out, M, S) <= FP32_TOL
+
+
+def test_sparse_cp_autograd():
+    spec = synth.small(4, 50_000, (1 << 12, 1 << 12, 1 << 8))
+    coords, vals, _ = make(spec)
+    A = [a.requires_grad_() for a in synth.factors(spec, rank=16, device="cuda", dist="normal")]
+    t = blco.Tensor.build(coords, vals, spec.dims)
+    sv = t.values()
+    xhat = blco.SparseCP.apply(t, *A)
+    loss = 0.5 * ((xhat - sv) ** 2).sum()
+    loss.backward()
+    resid = (xhat.detach() - sv).cpu().numpy().astype(np.float64)
+    c = coords.cpu().numpy()[t.perm()]
+    for n in range(3):
+        M, S = oracle.mttkrp(c, resid, spec.dims, to_np64([a.detach() for a in A]), n)
+        assert oracle.max_rel_err(A[n].grad.cpu().numpy(), M, S) <= FP32_TOL
+
+
+# ------------------------------------------------------------ CP-ALS (FP64 pieces)
+def test_gram_and_update_match_oracle():
+    rng = np.random.default_rng(3)
+    R = 16
+    A = [torch.from_numpy(rng.standard_normal((d, R)).astype(np.float32)).cuda() for d in (300, 200, 100)]
+    G = [torch.empty((R, R), dtype=torch.float64, device="cuda") for _ in A]
+    for a, g in zip(A, G):
+        blco.blco_gram(a, blco.BLCO_F32, a.shape[0], R, g)
+    for a, g in zip(A, G):
+        ref = oracle.gram(a.cpu().numpy().astype(np.float64))
+        np.testing.assert_allclose(g.cpu().numpy(), ref, rtol=1e-12, atol=1e-9)
+    M = torch.from_numpy(rng.standard_normal((300, R)).astype(np.float32)).cuda()
+    out = torch.empty_like(M)
+    lam = torch.empty(R, dtype=torch.float64, device="cuda")
+    Gn = torch.empty((R, R), dtype=torch.float64, device="cuda")
+    info = torch.zeros(1, dtype=torch.int32, device="cuda")
+    blco.blco_cpals_update(G, 3, 0, R, M, 300, out, lam, Gn, info)
+    V = oracle.gram(A[1].cpu().numpy().astype(np.float64)) * oracle.gram(A[2].cpu().numpy().astype(np.float64))
+    ref = oracle.cpals.solve_right(M.cpu().numpy().astype(np.float64), V)
+    lref = np.linalg.norm(ref, axis=0)
+    assert int(info.item()) == 0
+    np.testing.assert_allclose(lam.cpu().numpy(), lref, rtol=1e-5)
+    np.testing.assert_allclose(out.cpu().numpy(), ref / lref, rtol=1e-4, atol=1e-6)
+
+
+def test_update_pseudo_inverse_path():
+    R = 8
+    # rank-deficient Grams: identical columns make V singular
+    a = np.random.default_rng(4).standard_normal((50, R)).astype(np.float32)
+    a[:, 1] = a[:, 0]
+    A = torch.from_numpy(a).cuda()
+    G = torch.empty((R, R), dtype=torch.float64, device="cuda")
+    blco.blco_gram(A, blco.BLCO_F32, 50, R, G)
+    M = torch.from_numpy(np.random.default_rng(5).standard_normal((40, R)).astype(np.float32)).cuda()
+    out = torch.empty_like(M)
+    lam = torch.empty(R, dtype=torch.float64, device="cuda")
+    info = torch.zeros(1, dtype=torch.int32, device="cuda")
+    blco.blco_cpals_update([G, G], 2, 1, R, M, 40, out, lam, None, info)
+    assert int(info.item()) == 1
+    V = G.cpu().numpy()
+    ref = M.cpu().numpy().astype(np.float64) @ np.linalg.pinv(V, rcond=1e-10, hermitian=True)
+    lref = np.linalg.norm(ref, axis=0)
+    np.testing.assert_allclose(lam.cpu().numpy(), lref, rtol=1e-4)
+
+
+def test_cp_als_tracks_oracle_and_recovers_planted():
+    rng = np.random.default_rng(15)
+    dims = (30, 25, 20)
+    R = 8
+    P = [rng.standard_normal((d, R)) for d in dims]
+    import itertools
+    c = np.array(list(itertools.product(*[range(d) for d in dims])))
+    v = np.einsum("ir,jr,kr->ijk", *P)[tuple(c.T)]
+    t = blco.Tensor.build(torch.from_numpy(c.astype(np.int32)).cuda(), torch.from_numpy(v.astype(np.float32)).cuda(),
+                          dims)
+    init = [rng.standard_normal((d, R)) for d in dims]
+    A = [torch.from_numpy(a.astype(np.float32)).cuda() for a in init]
+    _, lam, fits = blco.cp_als(t, A, iters=60)
+    _, _, rfits = oracle.cp_als(c, v.astype(np.float32).astype(np.float64), dims,
+                                [a.astype(np.float32).astype(np.float64) for a in init], iters=60)
+    assert fits[-1] > 0.999
+    assert abs(fits[4] - rfits[4]) < 1e-3
