@@ -356,17 +356,17 @@ blco_status over_store(blco_tensor *h, const char *name, const float *vals_ext, 
     return BLCO_OK;
 }
 
+// Rows of `mode` accumulated on chip: every row when the mode fits, else the
+// mode's most frequent rows (by count).
 HotRows hot_for(const blco_tensor *h, int mode, int R) {
     HotRows hr;
-    const int cap = mttkrp_hot_capacity(R);
-    if (h->L.dims[mode] <= cap) {
+    hr.rows = h->d_hot[mode];
+    hr.count = h->hot_count[mode];
+    hr.dense = 0;
+    if (h->L.dims[mode] <= warp_tier_capacity(R)) {
         hr.rows = nullptr;
         hr.count = (int)h->L.dims[mode];
         hr.dense = 1;
-    } else {
-        hr.rows = h->d_hot[mode];
-        hr.count = std::min(h->hot_count[mode], cap);
-        hr.dense = 0;
     }
     return hr;
 }
@@ -489,7 +489,9 @@ blco_status blco_build(const uint32_t *coords, const float *vals, int64_t nnz, c
         const int64_t nb = (int64_t)h->bstart.size() - 1;
         bool zero_high = true;
         for (uint32_t v : h->bhigh) zero_high &= (v == 0);
-        h->single_block = nb <= 1 && zero_high;
+        // all-zero high bits (one block, or one block split at the cap): no
+        // per-tile block lookups are needed to de-linearize
+        h->single_block = zero_high;
         std::vector<uint32_t> bbase((size_t)std::max<int64_t>(nb, 1) * MAXN, 0u);
         for (int64_t b = 0; b < nb; ++b)
             for (int n = 0; n < N; ++n)

@@ -55,11 +55,11 @@ struct FactorSet {
     const void *ptr[MAXN];
 };
 
-// Hot output rows of one mode (accumulated in shared memory per CTA).
+// Hot output rows of one mode (accumulated in shared memory).
 struct HotRows {
-    const uint32_t *rows;  // row ids, sorted ascending (device)
-    int count;             // 0 = no on-chip accumulation
-    int dense;             // 1 = every row of the mode is hot (row id == slot)
+    const uint32_t *rows;  // row ids by decreasing count (device)
+    int count;             // rows available
+    int dense;             // 1 = every row of the mode is accumulated on chip (slot == row)
 };
 
 // ----------------------------------------------------------------- kernels
@@ -69,7 +69,8 @@ cudaError_t launch_mttkrp(const StoreView &sv, const FactorSet &fs, blco_dtype f
 cudaError_t launch_cp_fwd(const StoreView &sv, const FactorSet &fs, blco_dtype fdt, int R,
                           float *xhat, int64_t xhat_origin, cudaStream_t s);
 bool rank_supported(int R);
-int mttkrp_hot_capacity(int R);  // max hot rows per launch for rank R
+int mttkrp_hot_capacity(int R);  // max rows per launch accumulated on chip for rank R
+int warp_tier_capacity(int R);   // rows of the per-warp (read-modify-write) tier for rank R
 
 // build.cu
 struct BuildOut {

@@ -89,18 +89,25 @@ def generator(seed: int, device) -> torch.Generator:
 
 def _draw_mode(n: int, dim: int, dist: str, gen: torch.Generator, labels: Optional[torch.Tensor],
                cdf: Optional[torch.Tensor], device) -> torch.Tensor:
+    """n indices of one mode, int32 (every mode length here is below 2^31)."""
     if dist == "uniform":
-        return torch.randint(0, dim, (n,), generator=gen, device=device, dtype=torch.int64)
-    u = torch.rand(n, generator=gen, device=device, dtype=torch.float64)
-    rank = torch.searchsorted(cdf, u).clamp_(max=dim - 1)
-    return labels[rank]
+        return torch.randint(0, dim, (n,), generator=gen, device=device, dtype=torch.int32)
+    out = torch.empty(n, dtype=torch.int32, device=device)
+    chunk = 1 << 27
+    for a in range(0, n, chunk):
+        b = min(n, a + chunk)
+        u = torch.rand(b - a, generator=gen, device=device, dtype=torch.float64)
+        rank = torch.searchsorted(cdf, u).clamp_(max=dim - 1)
+        out[a:b] = labels[rank]
+        del u, rank
+    return out
 
 
 def _zipf_tables(dim: int, alpha: float, gen: torch.Generator, device):
     k = torch.arange(1, dim + 1, device=device, dtype=torch.float64)
     cdf = torch.cumsum(k.pow(-alpha), 0)
     cdf /= cdf[-1].clone()
-    labels = torch.randperm(dim, generator=gen, device=device)
+    labels = torch.randperm(dim, generator=gen, device=device).to(torch.int32)
     return labels, cdf
 
 
@@ -112,14 +119,15 @@ def _dedup_key(idx: torch.Tensor, dims: Sequence[int]) -> List[torch.Tensor]:
     words, cur, cur_bits = [], None, 0
     for k, d in enumerate(dims):
         b = max(1, math.ceil(math.log2(d))) if d > 1 else 1
+        col = idx[:, k].to(torch.int64)
         if cur is None:
-            cur, cur_bits = idx[:, k].clone(), b
+            cur, cur_bits = col, b
         elif cur_bits + b <= 62:
-            cur = cur * d + idx[:, k]
+            cur = cur * d + col
             cur_bits += b
         else:
             words.append(cur)
-            cur, cur_bits = idx[:, k].clone(), b
+            cur, cur_bits = col, b
     words.append(cur)
     return words
 
@@ -156,7 +164,7 @@ def coordinates(spec: TensorSpec, device="cpu", oversample: float = 1.15) -> tor
         total *= d
     if spec.nnz > total:
         raise ValueError("more nonzeros requested than the tensor has cells")
-    have = torch.empty((0, spec.order), dtype=torch.int64, device=device)
+    have = torch.empty((0, spec.order), dtype=torch.int32, device=device)
     want = int(spec.nnz * oversample) + 1024
     for _ in range(64):
         cols = [_draw_mode(want, d, dist, gen, lab, cdf, device)

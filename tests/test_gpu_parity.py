@@ -134,6 +134,25 @@ def test_mttkrp_positive_heavy_rows():
     check_mttkrp_all(t, coords, vals, A, spec.dims)
 
 
+@pytest.mark.parametrize("R", [16, 32, 64])
+@pytest.mark.parametrize("nrows", [1, 3, 40])
+def test_mttkrp_runs_across_subgroups(R, nrows):
+    """Every nonzero in one of a few rows of a long mode: the warp's sorted
+    runs cover whole subgroups and cross their boundaries."""
+    rng = np.random.default_rng(nrows * 100 + R)
+    dims = (100_000, 300, 200)
+    nnz = 50_000
+    rows = rng.choice(dims[0], nrows, replace=False)
+    c = np.stack([rng.choice(rows, nnz), rng.integers(0, dims[1], nnz), rng.integers(0, dims[2], nnz)], 1)
+    c = np.unique(c, axis=0)
+    rng.shuffle(c)
+    coords = torch.from_numpy(c.astype(np.int32)).cuda()
+    vals = torch.from_numpy(rng.random(len(c)).astype(np.float32)).cuda()
+    A = [torch.from_numpy(rng.random((d, R)).astype(np.float32)).cuda() for d in dims]  # positive terms
+    t = blco.Tensor.build(coords, vals, dims)
+    check_mttkrp_all(t, coords, vals, A, dims)
+
+
 @pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])
 def test_mttkrp_16bit_factors(dtype):
     spec = synth.small(2, 300_000, (1 << 14, 1 << 12, 1 << 10, 1 << 8))
