@@ -215,6 +215,29 @@ blco_status blco_cpals_update(const double *const *grams, int N, int mode, int R
                               blco_stream stream);
 
 /*
+ * blco_cpals_update_noalloc: the same update as blco_cpals_update (same
+ * arguments, same result) without allocating any device memory. The paper
+ * has no counterpart; it exists for callers that cannot let a library
+ * allocate during a call -- a process that reserved the GPU's memory up front
+ * for its own pool, or a latency-critical loop that cannot afford the
+ * device-wide synchronization of cudaFree. Its scratch (about 17 KB: the
+ * float32 inverse of V and two per-column vectors) is one fixed array in
+ * device memory that every GPU loading libblco.so holds until the process
+ * exits. Limits and behaviour:
+ *   - R must be in 1..64; larger ranks return BLCO_ERR_ARG.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) and caches it; make that first call before
+ *     capturing any stream work.
+ *   - Every call on a device uses the same scratch, which keeps the last
+ *     call's contents (the call clears what must start at zero). Calls whose
+ *     GPU work overlaps -- on different streams without ordering -- race on
+ *     it; order them on one stream or with events.
+ */
+blco_status blco_cpals_update_noalloc(const double *const *grams, int N, int mode, int R, const float *M,
+                                      int64_t I, float *A, double *lambda, double *G_out, int32_t *info,
+                                      blco_stream stream);
+
+/*
  * blco_cpals_fit: fit = 1 - ||X - Xhat|| / ||X|| of the model (lambda, A_1..A_N)
  * from ||X||^2 (host value), all N Grams, lambda, and the last mode's M and A:
  *   ||Xhat||^2 = lambda^T (Hadamard product of all Grams) lambda

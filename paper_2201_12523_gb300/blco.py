@@ -33,7 +33,7 @@ _DTYPE_CODE = {torch.float32: BLCO_F32, torch.bfloat16: BLCO_BF16, torch.float16
 EXPORTS = ["blco_default_opts", "blco_build", "blco_mttkrp", "blco_mttkrp_all", "blco_cp_fwd", "blco_cp_bwd",
            "blco_values", "blco_perm", "blco_keys", "blco_blocks", "blco_info", "blco_sync", "blco_destroy",
            "blco_last_error", "blco_convert", "blco_gram", "blco_cpals_update", "blco_cpals_fit", "blco_norm2",
-           "blco_profile_enable", "blco_profile_read"]
+           "blco_profile_enable", "blco_profile_read", "blco_cpals_update_noalloc"]
 
 
 class BuildOpts(ctypes.Structure):
@@ -86,6 +86,7 @@ def _load():
         "blco_convert": [vp, vp, i32, i64, vp],
         "blco_gram": [vp, i32, i64, i32, vp, vp],
         "blco_cpals_update": [vp, i32, i32, i32, vp, i64, vp, vp, vp, vp, vp],
+        "blco_cpals_update_noalloc": [vp, i32, i32, i32, vp, i64, vp, vp, vp, vp, vp],
         "blco_cpals_fit": [ctypes.c_double, vp, i32, i32, vp, vp, vp, i64, vp, vp],
         "blco_norm2": [vp, vp, vp],
         "blco_profile_enable": [vp, i32],
@@ -249,6 +250,15 @@ def blco_cpals_update(grams: Sequence, N: int, mode: int, R: int, M, I: int, A, 
     _check("blco_cpals_update", _lib.blco_cpals_update(_ptr_array(grams), int(N), int(mode), int(R), _ptr(M),
                                                        int(I), _ptr(A), _ptr(lam), _ptr(G_out), _ptr(info),
                                                        _stream(stream)))
+
+
+def blco_cpals_update_noalloc(grams: Sequence, N: int, mode: int, R: int, M, I: int, A, lam, G_out, info,
+                              stream=None):
+    """blco_cpals_update without any device allocation (fixed library
+    scratch, R <= 64); for callers that cannot let the library allocate."""
+    _check("blco_cpals_update_noalloc",
+           _lib.blco_cpals_update_noalloc(_ptr_array(grams), int(N), int(mode), int(R), _ptr(M), int(I), _ptr(A),
+                                          _ptr(lam), _ptr(G_out), _ptr(info), _stream(stream)))
 
 
 def blco_cpals_fit(normX2: float, grams: Sequence, N: int, R: int, lam, M_last, A_last, I_last: int, fit,

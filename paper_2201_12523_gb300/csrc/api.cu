@@ -952,4 +952,21 @@ blco_status blco_profile_read(blco_handle h, blco_profile_entry *entries, int ca
     return BLCO_OK;
 }
 
+blco_status blco_cpals_update_noalloc(const double *const *grams, int N, int mode, int R, const float *M,
+                                      int64_t I, float *A, double *lambda, double *G_out, int32_t *info,
+                                      blco_stream stream) {
+    g_err.clear();
+    if (!grams || !M || !A || !lambda || !info) return fail(BLCO_ERR_ARG, "NULL argument");
+    if (N < 1 || N > MAXN || mode < 0 || mode >= N) return fail(BLCO_ERR_ARG, "bad order or mode");
+    if (R < 1 || R > cpals_update_noalloc_max_rank())
+        return fail(BLCO_ERR_ARG, "rank exceeds the fixed scratch of blco_cpals_update_noalloc (R <= 64)");
+    if (I < 0) return fail(BLCO_ERR_ARG, "I < 0");
+    for (int k = 0; k < N; ++k)
+        if (k != mode && !grams[k]) return fail(BLCO_ERR_ARG, "grams[k] is NULL");
+    cudaError_t e = launch_cpals_update_noalloc(grams, N, mode, R, M, I, A, lambda, G_out, info,
+                                                reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "cpals_update_noalloc");
+    return BLCO_OK;
+}
+
 }  // extern "C"

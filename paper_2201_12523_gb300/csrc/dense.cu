@@ -5,6 +5,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <mutex>
+
 #include "internal.h"
 
 namespace blco {
@@ -440,6 +442,89 @@ cudaError_t launch_norm2(const float *v, int64_t n, double *out, cudaStream_t s)
 cudaError_t launch_norm2_acc(const float *v, int64_t n, double *out, cudaStream_t s) {
     if (n > 0) k_norm2<<<grid_cap(n, 256), 256, 0, s>>>(v, n, out);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// CP-ALS update without allocation.
+//
+// Some callers cannot let a library allocate device memory during a call:
+// a process that reserved the GPU's memory up front for its own pool (a
+// cudaMalloc would fail or escape its accounting), or a latency-critical loop
+// where the device-wide synchronization of cudaFree is not acceptable. For
+// them the update's scratch (the float32 inverse of V, the column sums of
+// squares and their reciprocals) lives in one file-scope device array that
+// every GPU which loads the library holds until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kNoAllocMaxRank = 64;
+constexpr size_t kNoAllocWfBytes = sizeof(float) * kNoAllocMaxRank * kNoAllocMaxRank;
+constexpr size_t kNoAllocColsqOff = (kNoAllocWfBytes + 255) & ~size_t(255);
+constexpr size_t kNoAllocInvOff = kNoAllocColsqOff + ((sizeof(double) * kNoAllocMaxRank + 255) & ~size_t(255));
+constexpr size_t kNoAllocScratchBytes = kNoAllocInvOff + sizeof(float) * kNoAllocMaxRank;
+
+// Shared by every call on a device; holds the previous call's contents.
+static __device__ __align__(256) unsigned char g_update_scratch[kNoAllocScratchBytes];
+
+std::mutex g_scratch_mutex;
+void *g_scratch_addr[64] = {};
+
+// Device address of g_update_scratch on the current device, looked up once
+// per device (the host-side name of the array is not a device address).
+cudaError_t update_scratch(unsigned char **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_update_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_addr[dev] = p;
+    }
+    *out = static_cast<unsigned char *>(g_scratch_addr[dev]);
+    return cudaSuccess;
+}
+
+}  // namespace
+
+int cpals_update_noalloc_max_rank() { return kNoAllocMaxRank; }
+
+cudaError_t launch_cpals_update_noalloc(const double *const *grams, int N, int mode, int R, const float *M,
+                                        int64_t I, float *A, double *lambda, double *G_out, int32_t *info,
+                                        cudaStream_t s) {
+    if (R < 1 || R > kNoAllocMaxRank) return cudaErrorInvalidValue;
+    unsigned char *base = nullptr;
+    cudaError_t e = update_scratch(&base);
+    if (e != cudaSuccess) return e;
+    float *Wf = reinterpret_cast<float *>(base);
+    double *colsq = reinterpret_cast<double *>(base + kNoAllocColsqOff);
+    float *inv = reinterpret_cast<float *>(base + kNoAllocInvOff);
+    GramPtrs gp;
+    for (int k = 0; k < MAXN; ++k) gp.g[k] = k < N ? grams[k] : nullptr;
+    const size_t shm_solve = sizeof(double) * 2 * R * R;
+    e = cudaFuncSetAttribute(k_solve_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_solve);
+    if (e != cudaSuccess) return e;
+    k_solve_small<<<1, 256, shm_solve, s>>>(gp, N, mode, R, Wf, info);
+    e = cudaGetLastError();
+    if (e == cudaSuccess && I > 0) {
+        const size_t shm = sizeof(float) * (R * R + 8 * R);
+        e = cudaFuncSetAttribute(k_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+        if (e == cudaSuccess) {
+            k_apply<<<grid_cap(I, 8), 256, shm, s>>>(M, I, R, Wf, A);
+            e = cudaGetLastError();
+        }
+    }
+    if (e == cudaSuccess) {
+        k_zero_d<<<1, 256, 0, s>>>(colsq, R);  // the shared scratch keeps the last call's sums
+        if (I > 0) k_colsq<<<grid_cap(I, 256 / R), 256, 0, s>>>(A, I, R, colsq);
+        k_sqrt_lambda<<<1, 128, 0, s>>>(colsq, R, lambda, inv);
+        if (I > 0) k_scale_cols<<<grid_cap(I * R, 256), 256, 0, s>>>(A, I, R, inv);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && G_out) e = launch_gram(A, BLCO_F32, I, R, G_out, s);
+    return e;
 }
 
 }  // namespace blco

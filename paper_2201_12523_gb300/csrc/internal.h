@@ -102,6 +102,10 @@ cudaError_t launch_cpals_update(const double *const *grams, int N, int mode, int
 cudaError_t launch_cpals_fit(double normX2, const double *const *grams, int N, int R,
                              const double *lambda, const float *M, const float *A, int64_t I,
                              double *fit, cudaStream_t s);
+cudaError_t launch_cpals_update_noalloc(const double *const *grams, int N, int mode, int R, const float *M,
+                                        int64_t I, float *A, double *lambda, double *G_out, int32_t *info,
+                                        cudaStream_t s);
+int cpals_update_noalloc_max_rank();
 cudaError_t launch_norm2(const float *v, int64_t n, double *out, cudaStream_t s);      // *out = sum v^2
 cudaError_t launch_norm2_acc(const float *v, int64_t n, double *out, cudaStream_t s);  // *out += sum v^2
 
