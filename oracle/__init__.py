@@ -57,6 +57,12 @@ def _load():
         _lib.orc_check_store.restype = ctypes.c_int64
         _lib.orc_check_store.argtypes = [ctypes.c_int64, ctypes.c_int, vp, vp, vp, ctypes.c_int,
                                          ctypes.c_int64, vp, vp, vp, ctypes.c_int64, vp, vp]
+        _lib.orc_check_store_at.restype = ctypes.c_int64
+        _lib.orc_check_store_at.argtypes = [ctypes.c_int64, ctypes.c_int, vp, vp, vp, ctypes.c_int,
+                                            ctypes.c_int64, vp, vp, vp, ctypes.c_int64, vp, vp,
+                                            ctypes.c_int64, vp]
+        _lib.orc_is_permutation.restype = ctypes.c_int
+        _lib.orc_is_permutation.argtypes = [ctypes.c_int64, vp]
         _lib.orc_mttkrp.restype = None
         _lib.orc_mttkrp.argtypes = [ctypes.c_int64, ctypes.c_int, vp, vp, vp, ctypes.c_int, vp,
                                     ctypes.c_int, vp, vp]
@@ -179,6 +185,27 @@ def check_store(coords, vals, dims, line_bits, max_nnz, keys, svals, perm, bstar
     return int(_load().orc_check_store(c.shape[0], c.shape[1], _p(c), _p(v), _p(d), int(line_bits),
                                        int(max_nnz), _p(keys), _p(svals), _p(perm),
                                        bstart.shape[0] - 1, _p(bstart), _p(bhigh)))
+
+
+def check_store_at(coords, vals, dims, line_bits, max_nnz, keys, svals, perm, bstart, bhigh, positions) -> int:
+    """The checks of check_store at the given store positions only (0 = pass)."""
+    c = _coords(coords)
+    v = np.ascontiguousarray(np.asarray(vals, dtype=np.float32))
+    d = _dims(dims)
+    keys = np.ascontiguousarray(np.asarray(keys, dtype=np.uint64))
+    svals = np.ascontiguousarray(np.asarray(svals, dtype=np.float32))
+    perm = np.ascontiguousarray(np.asarray(perm, dtype=np.int64))
+    bstart = np.ascontiguousarray(np.asarray(bstart, dtype=np.int64))
+    bhigh = np.ascontiguousarray(np.asarray(bhigh, dtype=np.uint32))
+    pos = np.ascontiguousarray(np.asarray(positions, dtype=np.int64))
+    return int(_load().orc_check_store_at(c.shape[0], c.shape[1], _p(c), _p(v), _p(d), int(line_bits),
+                                          int(max_nnz), _p(keys), _p(svals), _p(perm), bstart.shape[0] - 1,
+                                          _p(bstart), _p(bhigh), pos.shape[0], _p(pos)))
+
+
+def is_permutation(perm) -> bool:
+    p = np.ascontiguousarray(np.asarray(perm, dtype=np.int64))
+    return _load().orc_is_permutation(p.shape[0], _p(p)) == 1
 
 
 # --------------------------------------------------------------------------

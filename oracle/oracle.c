@@ -20,6 +20,9 @@
  *                     concatenated per-mode fields (mode 1 lowest).
  *   orc_check_store   the same definition checked against a given store in
  *                     one pass (for stores too large to rebuild here).
+ *   orc_check_store_at  the same checks at chosen store positions only (for
+ *                     stores too large for a full pass), plus
+ *   orc_is_permutation  whether a store's input positions are a permutation.
  *   orc_mttkrp        Eq. 1 evaluated per nonzero as in Fig. 3: fetch rows,
  *                     Hadamard product, scale by the value, accumulate into
  *                     row i_n; also S = sum of |terms| per output entry.
@@ -304,6 +307,85 @@ int64_t orc_check_store(int64_t nnz, int N, const uint32_t *coords, const float 
         }
     }
     if (b != nblocks || bstart[nblocks] != nnz) return -4;
+    return 0;
+}
+
+/* 1 if p[0..n) is a permutation of 0..n-1, else 0. */
+int orc_is_permutation(int64_t n, const int64_t *p) {
+    unsigned char *seen = (unsigned char *)calloc((size_t)(n / 8 + 1), 1);
+    if (!seen) return -1;
+    int ok = 1;
+    for (int64_t i = 0; i < n && ok; ++i) {
+        int64_t v = p[i];
+        if (v < 0 || v >= n || (seen[v >> 3] >> (v & 7)) & 1) ok = 0;
+        else seen[v >> 3] |= (unsigned char)(1u << (v & 7));
+    }
+    free(seen);
+    return ok;
+}
+
+/*
+ * The checks of orc_check_store at the store positions pos[0..npos): the
+ * entry is the re-encoded coordinate of its input row with that row's value;
+ * (linear index, input position) increases from the entry to the next one;
+ * the entry's block is the one bstart places it in, its high bits match, the
+ * block holds one block key from its first to its last entry, and no block is
+ * longer than the cap. Returns 0, or 1 + i for the first failing sample i, or
+ * -1 for bad arguments.
+ */
+int64_t orc_check_store_at(int64_t nnz, int N, const uint32_t *coords, const float *vals,
+                           const int64_t *dims, int line_bits, int64_t max_nnz,
+                           const uint64_t *skeys, const float *svals, const int64_t *sperm,
+                           int64_t nblocks, const int64_t *bstart, const uint32_t *bhigh,
+                           int64_t npos, const int64_t *pos) {
+    int bits[ORC_MAXN], kbits[ORC_MAXN], width[ORC_MAXN], shift[ORC_MAXN], km[128], kl[128];
+    if (line_bits < 1 || line_bits > 64 || max_nnz < 1) return -1;
+    int B = orc_fields(N, dims, line_bits, bits, kbits, width, shift, km, kl);
+    if (B < 0) return -1;
+    if (nblocks < 1 || bstart[0] != 0 || bstart[nblocks] != nnz) return -1;
+    for (int64_t i = 0; i < npos; ++i) {
+        const int64_t s = pos[i];
+        if (s < 0 || s >= nnz) return 1 + i;
+        const int64_t p = sperm[s];
+        if (p < 0 || p >= nnz) return 1 + i;
+        const uint32_t *c = coords + p * N;
+        for (int n = 0; n < N; ++n)
+            if ((int64_t)c[n] >= dims[n]) return 1 + i;
+        uint64_t key = 0;
+        for (int n = 0; n < N; ++n) {
+            uint64_t low = width[n] >= 64 ? (uint64_t)c[n] : ((uint64_t)c[n] & ((1ull << width[n]) - 1));
+            key |= low << shift[n];
+        }
+        if (skeys[s] != key) return 1 + i;
+        if (memcmp(&svals[s], &vals[p], sizeof(float)) != 0) return 1 + i;
+        uint64_t hi, lo;
+        orc_key_of(N, c, B, km, kl, &hi, &lo);
+        if (s + 1 < nnz) {
+            uint64_t h2, l2;
+            const uint32_t *c2 = coords + sperm[s + 1] * N;
+            orc_key_of(N, c2, B, km, kl, &h2, &l2);
+            int less = (hi < h2) || (hi == h2 && lo < l2) || (hi == h2 && lo == l2 && p < sperm[s + 1]);
+            if (!less) return 1 + i;
+        }
+        /* block of s: the last b with bstart[b] <= s */
+        int64_t a = 0, z = nblocks - 1;
+        while (a < z) {
+            int64_t m = (a + z + 1) / 2;
+            if (bstart[m] <= s) a = m;
+            else z = m - 1;
+        }
+        const int64_t b = a;
+        if (bstart[b + 1] - bstart[b] > max_nnz || bstart[b + 1] <= bstart[b]) return 1 + i;
+        for (int n = 0; n < N; ++n)
+            if (bhigh[b * N + n] != (uint32_t)((uint64_t)c[n] >> width[n])) return 1 + i;
+        uint64_t bh, bl, fh, fl, eh, el, h3, l3;
+        orc_block_key(hi, lo, line_bits, &bh, &bl);
+        orc_key_of(N, coords + sperm[bstart[b]] * N, B, km, kl, &h3, &l3);
+        orc_block_key(h3, l3, line_bits, &fh, &fl);
+        orc_key_of(N, coords + sperm[bstart[b + 1] - 1] * N, B, km, kl, &h3, &l3);
+        orc_block_key(h3, l3, line_bits, &eh, &el);
+        if (bh != fh || bl != fl || bh != eh || bl != el) return 1 + i;
+    }
     return 0;
 }
 

@@ -1,0 +1,188 @@
+"""Parity at the full workload sizes (10^8..10^9 nonzeros), in the launch
+configuration the benchmark uses, on outputs the FP64 oracle can compute one
+by one: the heaviest output rows of every mode plus random ones, sampled
+store positions, sampled CP model values. Properties that hold at any size
+(a permutation, sortedness at the samples, unit-norm CP-ALS columns, a fit
+that does not decrease) cover the rest."""
+
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2201_12523_gb300 import synth
+from tests._util import BF16_TOL, FP32_TOL, rounded16, to_np64
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+blco = pytest.importorskip("paper_2201_12523_gb300.blco")
+
+GB = 1 << 30
+
+
+def _host(coords, vals):
+    c = coords.cpu().numpy().view(np.uint32)
+    v = vals.cpu().numpy()
+    return c, v
+
+
+def _rows_to_check(col: np.ndarray, I: int, rng, n_top=8, n_rand=24):
+    counts = np.bincount(col, minlength=I)
+    top = np.argsort(counts)[::-1][:n_top]
+    rand = rng.choice(I, size=min(n_rand, I), replace=False)
+    return np.unique(np.concatenate([top, rand]))
+
+
+def _sampled_mttkrp(t, c, v64, dims, A, Af_ref, tol, seed, label):
+    rng = np.random.default_rng(seed)
+    errs = []
+    for n in range(len(dims)):
+        out = t.mttkrp(n, A)
+        torch.cuda.synchronize()
+        rows = _rows_to_check(c[:, n], dims[n], rng)
+        M, S = oracle.mttkrp_rows(c, v64, dims, Af_ref, n, rows)
+        got = out[torch.from_numpy(rows).cuda()].cpu().numpy()
+        err = oracle.max_rel_err(got, M, S)
+        errs.append(err)
+        print(f"{label} mode {n}: max rel err {err:.3e} over {len(rows)} rows")
+        assert err <= tol, f"{label} mode {n}: {err:.3e} > {tol:.1e}"
+    return errs
+
+
+def _store_samples(t, c, v, dims, line, cap, seed, n=20000):
+    keys = t.keys()
+    perm = t.perm()
+    svals = t.values(device="cpu").numpy()
+    bstart, bhigh = t.blocks()
+    assert oracle.is_permutation(perm)
+    rng = np.random.default_rng(seed)
+    pos = np.unique(np.concatenate([rng.integers(0, len(perm), n), bstart[:-1], bstart[1:] - 1,
+                                    [0, len(perm) - 1]]))
+    rc = oracle.check_store_at(c, v, dims, line, cap, keys, svals, perm, bstart, bhigh, pos)
+    assert rc == 0, f"store differs from the definition at sample {rc - 1}"
+    return perm
+
+
+# --------------------------------------------------------------- 150M, 3 modes
+def test_zipf3d_150M_store_and_mttkrp():
+    spec = synth.CONFIGS[1]
+    coords = synth.coordinates(spec, device="cuda")
+    vals = synth.values(spec, device="cuda")
+    A = synth.factors(spec, device="cuda")
+    torch.cuda.empty_cache()
+    t = blco.Tensor.build(coords, vals, spec.dims)
+    c, v = _host(coords, vals)
+    del coords, vals
+    # the whole store against the definition, in one pass
+    keys, perm = t.keys(), t.perm()
+    svals = t.values(device="cpu").numpy()
+    bstart, bhigh = t.blocks()
+    assert oracle.check_store(c, v, spec.dims, 64, 1 << 27, keys, svals, perm, bstart, bhigh) == 0
+    _sampled_mttkrp(t, c, v.astype(np.float64), spec.dims, A, to_np64(A), FP32_TOL, 1, "zipf3d f32")
+
+
+# --------------------------------------------------------------- 500M, 4 modes, BF16
+def test_zipf4d_500M_fp32_and_bf16():
+    spec = synth.CONFIGS[2]
+    coords = synth.coordinates(spec, device="cuda")
+    vals = synth.values(spec, device="cuda")
+    A = synth.factors(spec, device="cuda")
+    torch.cuda.empty_cache()
+    t = blco.Tensor.build(coords, vals, spec.dims)
+    c, v = _host(coords, vals)
+    del coords, vals
+    _store_samples(t, c, v, spec.dims, 64, 1 << 27, 2)
+    v64 = v.astype(np.float64)
+    Af = to_np64(A)
+    e32 = _sampled_mttkrp(t, c, v64, spec.dims, A, Af, FP32_TOL, 3, "zipf4d f32")
+    A16 = [blco.convert(a, torch.bfloat16) for a in A]
+    e16 = _sampled_mttkrp(t, c, v64, spec.dims, A16, Af, BF16_TOL, 3, "zipf4d bf16 vs unrounded")
+    e16r = _sampled_mttkrp(t, c, v64, spec.dims, A16, rounded16(A, torch.bfloat16), FP32_TOL, 3,
+                           "zipf4d bf16 vs rounded")
+    print("per-mode max rel err f32:", [f"{e:.2e}" for e in e32], "bf16:", [f"{e:.2e}" for e in e16],
+          "bf16 (rounded factors):", [f"{e:.2e}" for e in e16r])
+
+
+# --------------------------------------------------------------- 1B, 5 modes, streamed
+def test_zipf5d_1B_streamed_under_16GB():
+    spec = synth.CONFIGS[3]
+    coords = synth.coordinates(spec, device="cuda")
+    vals = synth.values(spec, device="cuda")
+    A = synth.factors(spec, device="cuda")
+    torch.cuda.empty_cache()
+    t = blco.Tensor.build(coords, vals, spec.dims, device_budget_bytes=16 * GB, force_stream=True)
+    info = t.info()
+    assert info["streamed"] and info["device_bytes"] <= 16 * GB
+    assert info["block_bits"] == [9, 5, 2, 0, 0] and info["nblocks"] > 1000
+    c, v = _host(coords, vals)
+    del coords, vals
+    torch.cuda.empty_cache()
+    _store_samples(t, c, v, spec.dims, 64, 1 << 27, 4)
+    _sampled_mttkrp(t, c, v.astype(np.float64), spec.dims, A, to_np64(A), FP32_TOL, 5, "5d streamed f32")
+
+
+# --------------------------------------------------------------- 200M, CP model
+def _planted_values(coords, P, sigma, seed):
+    """x = sum_r prod_n P_n[i_n, r] + N(0, sigma^2) (input synthesis, float64, chunked)."""
+    out = torch.empty(coords.shape[0], dtype=torch.float64, device="cuda")
+    Pd = [p.double() for p in P]
+    for a in range(0, coords.shape[0], 1 << 24):
+        b = min(coords.shape[0], a + (1 << 24))
+        cc = coords[a:b].long()
+        prod = Pd[0][cc[:, 0]]
+        for n in range(1, len(Pd)):
+            prod = prod * Pd[n][cc[:, n]]
+        out[a:b] = prod.sum(1)
+    return (out + synth.noise(coords.shape[0], sigma, seed, device="cuda").double()).float()
+
+
+def test_cp_planted_200M_fwd_bwd_and_als():
+    spec = synth.CONFIGS[4]
+    coords = synth.coordinates(spec, device="cuda")
+    P = synth.factors(spec, device="cuda", stream=5, dist="u01")          # planted rank-64 model
+    vals = _planted_values(coords, P, 0.01, spec.seed + 99)
+    del P
+    torch.cuda.empty_cache()
+    t = blco.Tensor.build(coords, vals, spec.dims)
+    c, v = _host(coords, vals)
+    del coords, vals
+    perm = t.perm()
+    rng = np.random.default_rng(6)
+    # forward: model values at sampled stored nonzeros, FP32 and BF16 factors
+    A = synth.factors(spec, device="cuda", stream=1, dist="normal")
+    pos = rng.choice(len(perm), 4096, replace=False)
+    cs = c[perm[pos]]
+    Af = to_np64(A)
+    ref, scale = oracle.cp_model(cs, Af), oracle.cp_model(cs, [np.abs(a) for a in Af])
+    for dt, tol in [(torch.float32, 1e-5), (torch.bfloat16, 1e-2)]:
+        Ad = A if dt == torch.float32 else [blco.convert(a, dt) for a in A]
+        xhat = t.cp_fwd(Ad).cpu().numpy()[pos]
+        err = float(np.max(np.abs(xhat - ref) / scale))
+        print(f"cp_fwd {dt}: max rel err {err:.3e}")
+        assert err <= tol
+    # adjoint: dL/dA_n for a seeded upstream gradient g (store order)
+    g = synth.noise(len(perm), 1.0, spec.seed + 7, device="cuda")
+    g64 = g.cpu().numpy().astype(np.float64)
+    cstore = c[perm]
+    for n in range(3):
+        out = t.cp_bwd(n, g, A)
+        rows = _rows_to_check(cstore[:, n], spec.dims[n], rng)
+        M, S = oracle.mttkrp_rows(cstore, g64, spec.dims, Af, n, rows)
+        err = oracle.max_rel_err(out[torch.from_numpy(rows).cuda()].cpu().numpy(), M, S)
+        print(f"cp_bwd mode {n}: max rel err {err:.3e}")
+        assert err <= FP32_TOL
+    del cstore
+    # 20 CP-ALS sweeps (MTTKRP in FP32, R x R algebra in FP64)
+    F = synth.factors(spec, device="cuda", stream=2, dist="u01")
+    t0 = time.perf_counter()
+    F, lam, fits = blco.cp_als(t, F, iters=20)
+    torch.cuda.synchronize()
+    print(f"CP-ALS 20 sweeps: {time.perf_counter() - t0:.2f} s, fits {fits[0]:.4f} -> {fits[-1]:.4f}")
+    assert all(b >= a - 1e-4 for a, b in zip(fits, fits[1:]))
+    assert fits[-1] > fits[0] and fits[-1] > 0.9
+    assert bool((lam > 0).all())
+    for f in F:
+        norms = torch.linalg.vector_norm(f.double(), dim=0).cpu().numpy()
+        np.testing.assert_allclose(norms, 1.0, rtol=1e-4)

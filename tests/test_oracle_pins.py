@@ -181,6 +181,32 @@ def test_check_store_accepts_and_rejects(orc):
             assert orc.check_store(*args, st.keys, st.svals, st.perm, st.bstart, h) != 0
 
 
+def test_sampled_store_check_accepts_and_rejects(orc):
+    rng = np.random.default_rng(31)
+    dims = (1 << 10, 1 << 8, 1 << 7, 33)
+    coords = np.unique(np.stack([rng.integers(0, d, 20000) for d in dims], 1), axis=0)
+    rng.shuffle(coords)
+    vals = rng.random(len(coords)).astype(np.float32)
+    line, cap = 20, 300
+    st = orc.build_store(coords, vals, dims, line, cap)
+    assert st.nblocks > 20
+    args = (coords, vals, dims, line, cap)
+    every = np.arange(len(coords))
+    assert orc.check_store_at(*args, st.keys, st.svals, st.perm, st.bstart, st.bhigh, every) == 0
+    assert orc.is_permutation(st.perm)
+    for s_bad in (0, 137, len(coords) - 1):
+        k = st.keys.copy(); k[s_bad] ^= np.uint64(4)
+        assert orc.check_store_at(*args, k, st.svals, st.perm, st.bstart, st.bhigh, [5, s_bad]) == 2
+    p = st.perm.copy(); p[[50, 51]] = p[[51, 50]]
+    assert orc.check_store_at(*args, st.keys, st.svals, p, st.bstart, st.bhigh, [50]) != 0
+    p[51] = p[52]
+    assert not orc.is_permutation(p)
+    h = st.bhigh.copy(); h[3, 0] ^= 1
+    assert orc.check_store_at(*args, st.keys, st.svals, st.perm, st.bstart, h, [int(st.bstart[3])]) != 0
+    b = st.bstart.copy(); b[4] -= 1
+    assert orc.check_store_at(*args, st.keys, st.svals, st.perm, b, st.bhigh, [int(b[4])]) != 0
+
+
 # ---------------------------------------------------------------- Eq. 1
 def _dense(coords, vals, dims):
     X = np.zeros(dims)
