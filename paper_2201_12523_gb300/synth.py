@@ -171,13 +171,15 @@ def coordinates(spec: TensorSpec, device="cpu", oversample: float = 1.15) -> tor
                 for d, dist, (lab, cdf) in zip(spec.dims, spec.index_dist, tables)]
         fresh = torch.stack(cols, 1)
         del cols
+        before = have.shape[0]
         have = _unique_rows(torch.cat([have, fresh], 0), spec.dims)
         del fresh
         if have.shape[0] >= spec.nnz:
             break
+        # draw enough for the missing count at this round's yield of new coordinates
         missing = spec.nnz - have.shape[0]
-        frac = have.shape[0] / max(1, want)
-        want = int(missing / max(frac, 0.05) * 1.3) + 1024
+        gained = (have.shape[0] - before) / max(1, want)
+        want = int(missing / max(gained, 0.01) * 1.3) + 1024
     else:  # pragma: no cover - only for absurd specs
         raise RuntimeError("could not draw enough distinct coordinates")
     pick = torch.randperm(have.shape[0], generator=gen, device=device)[: spec.nnz]

@@ -20,6 +20,13 @@ pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 blco = pytest.importorskip("paper_2201_12523_gb300.blco")
 
 GB = 1 << 30
+_T0 = [time.perf_counter()]
+
+
+def _tick(label):
+    now = time.perf_counter()
+    print(f"  [{now - _T0[0]:7.1f}s] {label}", flush=True)
+    _T0[0] = now
 
 
 def _host(coords, vals):
@@ -35,23 +42,34 @@ def _rows_to_check(col: np.ndarray, I: int, rng, n_top=8, n_rand=24):
     return np.unique(np.concatenate([top, rand]))
 
 
-def _sampled_mttkrp(t, c, v64, dims, A, Af_ref, tol, seed, label):
+def _pick_rows(c, dims, seed):
     rng = np.random.default_rng(seed)
+    return [_rows_to_check(np.ascontiguousarray(c[:, n]), dims[n], rng) for n in range(len(dims))]
+
+
+def _oracle_rows(c, v64, dims, Af_ref, rows):
+    out = []
+    for n in range(len(dims)):
+        out.append(oracle.mttkrp_rows(c, v64, dims, Af_ref, n, rows[n]))
+    _tick("oracle rows")
+    return out
+
+
+def _sampled_mttkrp(t, dims, A, rows, ref, tol, label):
     errs = []
     for n in range(len(dims)):
         out = t.mttkrp(n, A)
         torch.cuda.synchronize()
-        rows = _rows_to_check(c[:, n], dims[n], rng)
-        M, S = oracle.mttkrp_rows(c, v64, dims, Af_ref, n, rows)
-        got = out[torch.from_numpy(rows).cuda()].cpu().numpy()
+        M, S = ref[n]
+        got = out[torch.from_numpy(rows[n]).cuda()].cpu().numpy()
         err = oracle.max_rel_err(got, M, S)
         errs.append(err)
-        print(f"{label} mode {n}: max rel err {err:.3e} over {len(rows)} rows")
+        print(f"{label} mode {n}: max rel err {err:.3e} over {len(rows[n])} rows")
         assert err <= tol, f"{label} mode {n}: {err:.3e} > {tol:.1e}"
     return errs
 
 
-def _store_samples(t, c, v, dims, line, cap, seed, n=20000):
+def _store_samples(t, c, v, dims, line, cap, seed, n=200000):
     keys = t.keys()
     perm = t.perm()
     svals = t.values(device="cpu").numpy()
@@ -62,56 +80,66 @@ def _store_samples(t, c, v, dims, line, cap, seed, n=20000):
                                     [0, len(perm) - 1]]))
     rc = oracle.check_store_at(c, v, dims, line, cap, keys, svals, perm, bstart, bhigh, pos)
     assert rc == 0, f"store differs from the definition at sample {rc - 1}"
+    _tick(f"store checked at {len(pos)} positions, permutation checked")
     return perm
 
 
 # --------------------------------------------------------------- 150M, 3 modes
 def test_zipf3d_150M_store_and_mttkrp():
+    _tick("start")
     spec = synth.CONFIGS[1]
     coords = synth.coordinates(spec, device="cuda")
     vals = synth.values(spec, device="cuda")
     A = synth.factors(spec, device="cuda")
     torch.cuda.empty_cache()
+    _tick("generated")
     t = blco.Tensor.build(coords, vals, spec.dims)
     c, v = _host(coords, vals)
     del coords, vals
-    # the whole store against the definition, in one pass
-    keys, perm = t.keys(), t.perm()
-    svals = t.values(device="cpu").numpy()
-    bstart, bhigh = t.blocks()
-    assert oracle.check_store(c, v, spec.dims, 64, 1 << 27, keys, svals, perm, bstart, bhigh) == 0
-    _sampled_mttkrp(t, c, v.astype(np.float64), spec.dims, A, to_np64(A), FP32_TOL, 1, "zipf3d f32")
+    _tick("built")
+    _store_samples(t, c, v, spec.dims, 64, 1 << 27, 1, n=1_000_000)
+    rows = _pick_rows(c, spec.dims, 1)
+    ref = _oracle_rows(c, v.astype(np.float64), spec.dims, to_np64(A), rows)
+    _sampled_mttkrp(t, spec.dims, A, rows, ref, FP32_TOL, "zipf3d f32")
+    _tick("done")
 
 
 # --------------------------------------------------------------- 500M, 4 modes, BF16
 def test_zipf4d_500M_fp32_and_bf16():
+    _tick("start")
     spec = synth.CONFIGS[2]
     coords = synth.coordinates(spec, device="cuda")
     vals = synth.values(spec, device="cuda")
     A = synth.factors(spec, device="cuda")
     torch.cuda.empty_cache()
+    _tick("generated")
     t = blco.Tensor.build(coords, vals, spec.dims)
     c, v = _host(coords, vals)
     del coords, vals
+    _tick("built")
     _store_samples(t, c, v, spec.dims, 64, 1 << 27, 2)
     v64 = v.astype(np.float64)
-    Af = to_np64(A)
-    e32 = _sampled_mttkrp(t, c, v64, spec.dims, A, Af, FP32_TOL, 3, "zipf4d f32")
+    rows = _pick_rows(c, spec.dims, 3)
+    ref32 = _oracle_rows(c, v64, spec.dims, to_np64(A), rows)
+    ref16 = _oracle_rows(c, v64, spec.dims, rounded16(A, torch.bfloat16), rows)
+    e32 = _sampled_mttkrp(t, spec.dims, A, rows, ref32, FP32_TOL, "zipf4d f32")
     A16 = [blco.convert(a, torch.bfloat16) for a in A]
-    e16 = _sampled_mttkrp(t, c, v64, spec.dims, A16, Af, BF16_TOL, 3, "zipf4d bf16 vs unrounded")
-    e16r = _sampled_mttkrp(t, c, v64, spec.dims, A16, rounded16(A, torch.bfloat16), FP32_TOL, 3,
-                           "zipf4d bf16 vs rounded")
+    e16 = _sampled_mttkrp(t, spec.dims, A16, rows, ref32, BF16_TOL, "zipf4d bf16 vs unrounded")
+    e16r = _sampled_mttkrp(t, spec.dims, A16, rows, ref16, FP32_TOL, "zipf4d bf16 vs rounded")
     print("per-mode max rel err f32:", [f"{e:.2e}" for e in e32], "bf16:", [f"{e:.2e}" for e in e16],
           "bf16 (rounded factors):", [f"{e:.2e}" for e in e16r])
+    _tick("done")
 
 
 # --------------------------------------------------------------- 1B, 5 modes, streamed
 def test_zipf5d_1B_streamed_under_16GB():
+    _tick("start")
     spec = synth.CONFIGS[3]
     coords = synth.coordinates(spec, device="cuda")
     vals = synth.values(spec, device="cuda")
     A = synth.factors(spec, device="cuda")
     torch.cuda.empty_cache()
+    _tick("generated")
     t = blco.Tensor.build(coords, vals, spec.dims, device_budget_bytes=16 * GB, force_stream=True)
     info = t.info()
     assert info["streamed"] and info["device_bytes"] <= 16 * GB
@@ -119,8 +147,12 @@ def test_zipf5d_1B_streamed_under_16GB():
     c, v = _host(coords, vals)
     del coords, vals
     torch.cuda.empty_cache()
+    _tick("built")
     _store_samples(t, c, v, spec.dims, 64, 1 << 27, 4)
-    _sampled_mttkrp(t, c, v.astype(np.float64), spec.dims, A, to_np64(A), FP32_TOL, 5, "5d streamed f32")
+    rows = _pick_rows(c, spec.dims, 5)
+    ref = _oracle_rows(c, v.astype(np.float64), spec.dims, to_np64(A), rows)
+    _sampled_mttkrp(t, spec.dims, A, rows, ref, FP32_TOL, "5d streamed f32")
+    _tick("done")
 
 
 # --------------------------------------------------------------- 200M, CP model
@@ -139,6 +171,7 @@ def _planted_values(coords, P, sigma, seed):
 
 
 def test_cp_planted_200M_fwd_bwd_and_als():
+    _tick("start")
     spec = synth.CONFIGS[4]
     coords = synth.coordinates(spec, device="cuda")
     P = synth.factors(spec, device="cuda", stream=5, dist="u01")          # planted rank-64 model
@@ -150,6 +183,7 @@ def test_cp_planted_200M_fwd_bwd_and_als():
     del coords, vals
     perm = t.perm()
     rng = np.random.default_rng(6)
+    _tick("generated and built")
     # forward: model values at sampled stored nonzeros, FP32 and BF16 factors
     A = synth.factors(spec, device="cuda", stream=1, dist="normal")
     pos = rng.choice(len(perm), 4096, replace=False)
@@ -174,6 +208,7 @@ def test_cp_planted_200M_fwd_bwd_and_als():
         print(f"cp_bwd mode {n}: max rel err {err:.3e}")
         assert err <= FP32_TOL
     del cstore
+    _tick("forward and adjoint checked")
     # 20 CP-ALS sweeps (MTTKRP in FP32, R x R algebra in FP64)
     F = synth.factors(spec, device="cuda", stream=2, dist="u01")
     t0 = time.perf_counter()
