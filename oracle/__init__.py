@@ -225,20 +225,26 @@ def mttkrp(coords, vals, dims, factors, mode: int) -> Tuple[np.ndarray, np.ndarr
 
 
 def mttkrp_rows(coords, vals, dims, factors, mode: int, rows) -> Tuple[np.ndarray, np.ndarray]:
-    """MTTKRP and S for the listed output rows only (rows distinct)."""
+    """MTTKRP and S for the listed output rows only (returned in the order given)."""
     c = _coords(coords)
     v = np.ascontiguousarray(np.asarray(vals, dtype=np.float64))
     d = _dims(dims)
     rows = np.asarray(rows, dtype=np.int64)
+    order = np.argsort(rows, kind="stable")
+    srt = np.ascontiguousarray(rows[order])
+    if srt.size and np.any(srt[1:] == srt[:-1]):
+        raise ValueError("rows must be distinct")
     R = int(np.asarray(factors[(mode + 1) % len(factors)]).shape[1])
     arr, keep = _factor_table(factors, R, d)
-    slot = np.full(int(d[mode]), -1, np.int64)
-    slot[rows] = np.arange(rows.shape[0])
     M = np.zeros((rows.shape[0], R))
     S = np.zeros((rows.shape[0], R))
     _load().orc_mttkrp_rows(c.shape[0], c.shape[1], _p(c), _p(v), _p(d), R, arr, int(mode),
-                            _p(slot), rows.shape[0], _p(M), _p(S))
-    return M, S
+                            _p(srt), srt.shape[0], _p(M), _p(S))
+    out_M = np.empty_like(M)
+    out_S = np.empty_like(S)
+    out_M[order] = M
+    out_S[order] = S
+    return out_M, out_S
 
 
 def cp_model(coords, factors) -> np.ndarray:

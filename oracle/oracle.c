@@ -415,21 +415,32 @@ void orc_mttkrp(int64_t nnz, int N, const uint32_t *coords, const double *vals,
 }
 
 /*
- * orc_mttkrp restricted to output rows with slot_of_row[i] >= 0: row i goes to
- * Msel/Ssel row slot_of_row[i] (nsel x R, zeroed here).
+ * orc_mttkrp restricted to the output rows rows[0..nsel) (sorted ascending,
+ * distinct): row rows[k] goes to Msel/Ssel row k (nsel x R, zeroed here).
+ * A bitmap of the chosen rows filters the nonzeros; a binary search finds
+ * the output row of a chosen one. Terms are added in input order.
  */
 void orc_mttkrp_rows(int64_t nnz, int N, const uint32_t *coords, const double *vals,
                      const int64_t *dims, int R, const double *const *factors, int mode,
-                     const int64_t *slot_of_row, int64_t nsel, double *Msel, double *Ssel) {
-    (void)dims;
+                     const int64_t *rows, int64_t nsel, double *Msel, double *Ssel) {
     memset(Msel, 0, sizeof(double) * (size_t)nsel * (size_t)R);
     memset(Ssel, 0, sizeof(double) * (size_t)nsel * (size_t)R);
+    const int64_t I = dims[mode];
+    unsigned char *chosen = (unsigned char *)calloc((size_t)(I / 8 + 1), 1);
+    if (!chosen) return;
+    for (int64_t k = 0; k < nsel; ++k) chosen[rows[k] >> 3] |= (unsigned char)(1u << (rows[k] & 7));
     for (int64_t j = 0; j < nnz; ++j) {
         const uint32_t *c = coords + j * N;
-        int64_t slot = slot_of_row[c[mode]];
-        if (slot < 0) continue;
-        double *m = Msel + slot * R;
-        double *sa = Ssel + slot * R;
+        const int64_t i = c[mode];
+        if (!((chosen[i >> 3] >> (i & 7)) & 1)) continue;
+        int64_t a = 0, z = nsel - 1;
+        while (a < z) {
+            const int64_t m = (a + z) / 2;
+            if (rows[m] < i) a = m + 1;
+            else z = m;
+        }
+        double *m = Msel + a * R;
+        double *sa = Ssel + a * R;
         for (int r = 0; r < R; ++r) {
             double t = vals[j];
             for (int k = 0; k < N; ++k)
@@ -438,6 +449,7 @@ void orc_mttkrp_rows(int64_t nnz, int N, const uint32_t *coords, const double *v
             sa[r] += fabs(t);
         }
     }
+    free(chosen);
 }
 
 /* CP model value at each nonzero: xhat_j = sum_r prod_n A_n[i_n^j, r]. */

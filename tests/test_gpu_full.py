@@ -215,8 +215,10 @@ def test_cp_planted_200M_fwd_bwd_and_als():
     F, lam, fits = blco.cp_als(t, F, iters=20)
     torch.cuda.synchronize()
     print(f"CP-ALS 20 sweeps: {time.perf_counter() - t0:.2f} s, fits {fits[0]:.4f} -> {fits[-1]:.4f}")
+    # the zeros of the sparse tensor count in the fit, so a model planted at
+    # 2e8 of 2^50 cells does not make a low-rank tensor: check properties
     assert all(b >= a - 1e-4 for a, b in zip(fits, fits[1:]))
-    assert fits[-1] > fits[0] and fits[-1] > 0.9
+    assert fits[-1] > fits[0]
     assert bool((lam > 0).all())
     for f in F:
         norms = torch.linalg.vector_norm(f.double(), dim=0).cpu().numpy()
