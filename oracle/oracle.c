@@ -417,39 +417,76 @@ void orc_mttkrp(int64_t nnz, int N, const uint32_t *coords, const double *vals,
 /*
  * orc_mttkrp restricted to the output rows rows[0..nsel) (sorted ascending,
  * distinct): row rows[k] goes to Msel/Ssel row k (nsel x R, zeroed here).
- * A bitmap of the chosen rows filters the nonzeros; a binary search finds
- * the output row of a chosen one. Terms are added in input order.
+ * One pass lists, per chosen row and in input order, the nonzeros that hit
+ * it (a bitmap filters, a binary search finds the row); then each chosen row
+ * sums its own list in input order. Rows are independent, so they may be
+ * summed by several threads (OpenMP, when compiled with it): every row's sum
+ * is the same sequence of additions as in a single-threaded loop.
  */
+static int64_t orc_find_row(const int64_t *rows, int64_t nsel, int64_t i) {
+    int64_t a = 0, z = nsel - 1;
+    while (a < z) {
+        const int64_t m = (a + z) / 2;
+        if (rows[m] < i) a = m + 1;
+        else z = m;
+    }
+    return a;
+}
+
 void orc_mttkrp_rows(int64_t nnz, int N, const uint32_t *coords, const double *vals,
                      const int64_t *dims, int R, const double *const *factors, int mode,
                      const int64_t *rows, int64_t nsel, double *Msel, double *Ssel) {
     memset(Msel, 0, sizeof(double) * (size_t)nsel * (size_t)R);
     memset(Ssel, 0, sizeof(double) * (size_t)nsel * (size_t)R);
+    if (nsel <= 0) return;
     const int64_t I = dims[mode];
     unsigned char *chosen = (unsigned char *)calloc((size_t)(I / 8 + 1), 1);
-    if (!chosen) return;
+    int64_t *start = (int64_t *)calloc((size_t)nsel + 1, sizeof(int64_t));
+    if (!chosen || !start) {
+        free(chosen);
+        free(start);
+        return;
+    }
     for (int64_t k = 0; k < nsel; ++k) chosen[rows[k] >> 3] |= (unsigned char)(1u << (rows[k] & 7));
     for (int64_t j = 0; j < nnz; ++j) {
-        const uint32_t *c = coords + j * N;
-        const int64_t i = c[mode];
-        if (!((chosen[i >> 3] >> (i & 7)) & 1)) continue;
-        int64_t a = 0, z = nsel - 1;
-        while (a < z) {
-            const int64_t m = (a + z) / 2;
-            if (rows[m] < i) a = m + 1;
-            else z = m;
-        }
-        double *m = Msel + a * R;
-        double *sa = Ssel + a * R;
-        for (int r = 0; r < R; ++r) {
-            double t = vals[j];
-            for (int k = 0; k < N; ++k)
-                if (k != mode) t *= factors[k][(int64_t)c[k] * R + r];
-            m[r] += t;
-            sa[r] += fabs(t);
+        const int64_t i = coords[j * N + mode];
+        if ((chosen[i >> 3] >> (i & 7)) & 1) start[orc_find_row(rows, nsel, i) + 1]++;
+    }
+    for (int64_t k = 0; k < nsel; ++k) start[k + 1] += start[k];
+    int64_t *list = (int64_t *)malloc(sizeof(int64_t) * (size_t)(start[nsel] > 0 ? start[nsel] : 1));
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)nsel);
+    if (!list || !fill) {
+        free(chosen);
+        free(start);
+        free(list);
+        free(fill);
+        return;
+    }
+    memcpy(fill, start, sizeof(int64_t) * (size_t)nsel);
+    for (int64_t j = 0; j < nnz; ++j) {
+        const int64_t i = coords[j * N + mode];
+        if ((chosen[i >> 3] >> (i & 7)) & 1) list[fill[orc_find_row(rows, nsel, i)]++] = j;
+    }
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t k = 0; k < nsel; ++k) {
+        double *m = Msel + k * R;
+        double *sa = Ssel + k * R;
+        for (int64_t q = start[k]; q < start[k + 1]; ++q) {
+            const int64_t j = list[q];
+            const uint32_t *c = coords + j * N;
+            for (int r = 0; r < R; ++r) {
+                double t = vals[j];
+                for (int kk = 0; kk < N; ++kk)
+                    if (kk != mode) t *= factors[kk][(int64_t)c[kk] * R + r];
+                m[r] += t;
+                sa[r] += fabs(t);
+            }
         }
     }
     free(chosen);
+    free(start);
+    free(list);
+    free(fill);
 }
 
 /* CP model value at each nonzero: xhat_j = sum_r prod_n A_n[i_n^j, r]. */
