@@ -198,7 +198,7 @@ def cpu_oracle_rate(spec, coords, vals, A, sample_nnz: int, repeats: int = 1):
     import oracle
 
     oracle.build()
-    c = coords[:sample_nnz].cpu().numpy().astype(np.uint32)
+    c = coords[:sample_nnz].cpu().numpy().view(np.uint32)
     v = vals[:sample_nnz].cpu().numpy().astype(np.float64)
     Af = [a.cpu().numpy().astype(np.float64) for a in A]
     times = []
@@ -264,6 +264,43 @@ def time_steps(step, K: int, stream) -> float:
     return e0.elapsed_time(e1)
 
 
+STREAMED = {"zipf1.2-5d-1B": 16 << 30}  # workloads run out of core: device budget in bytes
+CP_MODEL = "cp-planted-3d-200M"
+
+
+def host_link_gbs(dev, nbytes=2 << 30, reps=5) -> float:
+    """Pinned host -> device copy bandwidth (GB/s), the out-of-memory bound."""
+    src = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    dst = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    dst.copy_(src, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        dst.copy_(src, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    gbs = nbytes * reps / (e0.elapsed_time(e1) / 1e3) / 1e9
+    del src, dst
+    return gbs
+
+
+def planted_store(blco, spec, coords, dev):
+    """Store of the planted CP workload: values = the CP model of seeded U(0,1)
+    factors at the coordinates (computed with the library's own forward kernel
+    on a provisional store) plus N(0, 0.01) noise."""
+    P = synth.factors(spec, device=dev, stream=5, dist="u01")
+    tmp = blco.Tensor.build(coords, torch.zeros(coords.shape[0], device=dev), spec.dims)
+    xhat = tmp.cp_fwd(P)
+    perm = torch.from_numpy(tmp.perm()).to(dev)
+    tmp.destroy()
+    vals = torch.empty_like(xhat)
+    vals[perm] = xhat
+    vals += synth.noise(coords.shape[0], 0.01, spec.seed + 99, device=dev)
+    del P, xhat, perm
+    return vals
+
+
 def run_blco(args, ranks: Ranks):
     from paper_2201_12523_gb300 import blco
 
@@ -272,29 +309,56 @@ def run_blco(args, ranks: Ranks):
     spec = WORKLOADS[args.workload]
     if args.nnz:
         spec = spec.scaled(args.nnz, spec.dims, name=f"{spec.name}@{args.nnz}")
+    base_name = args.workload
     R = spec.rank
     t_gen = time.perf_counter()
     coords, vals, A = gen_inputs(spec, dev)
+    if base_name == CP_MODEL:
+        vals = planted_store(blco, spec, coords, dev)
+        A = synth.factors(spec, device=dev, stream=1, dist="normal")
     torch.cuda.synchronize()
     gen_s = time.perf_counter() - t_gen
     torch.cuda.empty_cache()
 
+    budget = STREAMED.get(base_name, 0)
     stream = torch.cuda.current_stream()
     eb0, eb1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     eb0.record(stream)
-    t = blco.Tensor.build(coords, vals, spec.dims)
+    t = blco.Tensor.build(coords, vals, spec.dims, device_budget_bytes=budget, force_stream=bool(budget))
     eb1.record(stream)
     torch.cuda.synchronize()
     build_ms = eb0.elapsed_time(eb1)
     info = t.info()
+    coords_h = coords[: min(spec.nnz, 1_000_000)].cpu()
+    vals_h = vals[: min(spec.nnz, 1_000_000)].cpu()
+    del coords, vals
+    torch.cuda.empty_cache()
 
     outs = [torch.empty((d, R), dtype=torch.float32, device=dev) for d in spec.dims]
 
-    def make_step(factors):
-        def step():
-            for n in range(spec.order):
-                t.mttkrp(n, factors, out=outs[n])
-        return step
+    if base_name == CP_MODEL:
+        sv = t.values()
+        grads = [torch.empty((d, R), dtype=torch.float32, device=dev) for d in spec.dims]
+
+        def make_step(factors):
+            def step():
+                # the sparse CP model at the nonzeros and the adjoint of a
+                # least-squares loss for every factor (one kernel each)
+                xhat = t.cp_fwd(factors)
+                g = xhat - sv
+                for n in range(spec.order):
+                    t.cp_bwd(n, g, factors, out=grads[n])
+            return step
+        metric = "sparse CP forward + adjoint (all factors) throughput"
+        kernel_kinds = ("mttkrp", "cp_fwd")
+    else:
+        def make_step(factors):
+            def step():
+                for n in range(spec.order):
+                    t.mttkrp(n, factors, out=outs[n])
+            return step
+        metric = "all-mode sparse MTTKRP throughput"
+        kernel_kinds = ("mttkrp",)
 
     step32 = make_step(A)
     for _ in range(args.warmup):
@@ -319,19 +383,46 @@ def run_blco(args, ranks: Ranks):
     peak, peak_src = hbm_peak()
     launches, kms = prof.get("mttkrp", (0, 0.0))
     zl, zms = prof.get("zero", (0, 0.0))
+    fl, fms = prof.get("cp_fwd", (0, 0.0))
     bytes_all = sum(algorithmic_bytes(spec, R, 4, n) for n in range(spec.order))
     per_launch_bytes = bytes_all / spec.order
     per_launch_ms = kms / max(launches, 1)
     achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9 if launches else None
     traffic = None
-    if TRAFFIC_RECORD["mttkrp_src_sha256"] == mttkrp_src_sha():
+    if TRAFFIC_RECORD["mttkrp_src_sha256"] == mttkrp_src_sha() and base_name == DEFAULT_WORKLOAD and not args.nnz:
         traffic = TRAFFIC_RECORD["bytes_per_launch"]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                "kernel": "k_mttkrp<float,32>", "peak_source": peak_src + " (burst copy, MEASURED_PEAKS hbm_gbs)",
+                "kernel": f"k_mttkrp<float,{R},{spec.order - 1}>",
+                "peak_source": peak_src + " (burst copy, MEASURED_PEAKS hbm_gbs)",
                 "algorithmic_bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_ms}
+    if info["streamed"]:
+        roofline["note"] = ("streamed store: kernel time measured on the queue streams; the step is bound by "
+                            "the host link (see host_link)")
 
     extra = {}
+    if info["streamed"]:
+        link = host_link_gbs(dev)
+        moved = 12 * spec.nnz * spec.order  # keys + values cross the link once per mode
+        achieved_link = moved / (ms_per_step / 1e3) / 1e9
+        extra["host_link"] = {"achieved": achieved_link, "peak": link, "unit": "GB/s",
+                              "frac": achieved_link / link, "bytes_per_step": moved,
+                              "peak_source": "pinned cudaMemcpyAsync H2D, 2 GiB x 5, same run"}
+        extra["store"] = "pinned host memory, %d queues x %d nonzeros, device budget %d GiB" % (
+            info["n_queues"], info["queue_nnz"], budget >> 30)
+    if base_name == CP_MODEL:
+        extra["cp_fwd_ms_per_launch"] = fms / max(fl, 1)
+        extra["adjoint_ms_per_launch"] = per_launch_ms
+        Fals = synth.factors(spec, device=dev, stream=2, dist="u01")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, _, fits = blco.cp_als(t, Fals, iters=20)
+        torch.cuda.synchronize()
+        extra["cp_als"] = {"sweeps": 20, "s_per_sweep": (time.perf_counter() - t0) / 20,
+                           "fit_first": fits[0], "fit_last": fits[-1],
+                           "note": "MTTKRP in FP32, Gram Hadamard / Cholesky / fit in FP64 on the GPU"}
+        del Fals
+
     # bfloat16 factors, same step
     if not args.no_bf16:
         A16 = [blco.convert(a, torch.bfloat16) for a in A]
@@ -350,9 +441,9 @@ def run_blco(args, ranks: Ranks):
                          "error_bound": 1e-2, "error_vs": "FP64 oracle on the unrounded float32 factors"}
         del A16
 
-    # end to end through the C ABI with host buffers
+    # end to end through the C ABI with host buffers (MTTKRP workloads)
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and base_name != CP_MODEL:
         Ah = [a.cpu().pin_memory() for a in A]
         Oh = [torch.empty((d, R), dtype=torch.float32).pin_memory() for d in spec.dims]
         Ah_np = [a.numpy() for a in Ah]
@@ -373,28 +464,33 @@ def run_blco(args, ranks: Ranks):
         d2h = h2d
         e2e = {"value": ranks.sum(spec.nnz) / sec, "unit": "nnz/s (all-mode)", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": sec * 1e3, "steps": K2,
-               "note": "blco_mttkrp_all with pinned host factors and host results; store resident"}
+               "note": "blco_mttkrp_all with pinned host factors and host results; store built once"}
 
     cpu = None
     if not args.no_cpu and ranks.rank == 0:
         sample = min(spec.nnz, 1_000_000)
-        rate, sec = cpu_oracle_rate(spec, coords, vals, A, sample)
+        rate, sec = cpu_oracle_rate(spec, coords_h, vals_h, A, sample)
         cpu = {"value": rate, "unit": "nnz/s (all-mode)", "cores": 1, "kind": "oracle",
                "sample": f"first {sample} nonzeros of the workload (random order), all {spec.order} modes, "
                          f"FP64 C loops, one thread, {sec:.2f} s"}
 
-    line = {"metric": "all-mode sparse MTTKRP throughput", "value": value, "unit": "nnz/s (all-mode)",
+    dists = sorted(set(spec.index_dist))
+    line = {"metric": metric, "value": value, "unit": "nnz/s (all-mode)",
             "n_gpus": ranks.world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": spec.name, "dims": list(spec.dims), "nnz": spec.nnz, "rank": R,
-                       "factors": "float32 N(0,1)", "values": "U(0,1)", "index_dist": "Zipf(1.2), permuted labels",
+                       "factors": "float32 " + ("N(0,1)" if spec.factor_dist == "normal" or base_name == CP_MODEL
+                                                 else "U(0,1)"),
+                       "values": spec.value_dist if base_name != CP_MODEL else "planted rank-64 CP + N(0,0.01)",
+                       "index_dist": ",".join(dists) + " (Zipf labels permuted)",
                        "parallelism": f"replicas x{ranks.world}",
-                       "l2": "inputs larger than L2 (store 1.8 GB + factors 0.8 GB), no flush"},
+                       "l2": "inputs larger than L2, no flush"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": int(launches + zl),
-            "build_ms": build_ms, "gen_s": gen_s, "store": {"nblocks": info["nblocks"], "hot_rows": info["hot_rows"],
-                                                          "device_bytes": info["device_bytes"]}}
+            "gpu_launches": int(launches + zl + fl),
+            "build_ms": build_ms, "gen_s": gen_s,
+            "store": {"nblocks": info["nblocks"], "streamed": info["streamed"], "hot_rows": info["hot_rows"],
+                      "device_bytes": info["device_bytes"]}}
     line.update(extra)
     if ranks.rank == 0:
         print(json.dumps(line), flush=True)
