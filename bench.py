@@ -105,6 +105,11 @@ class Ranks:
         if self.pg is not None:
             self.pg.destroy_process_group()
 
+    def rate(self, units: float, seconds: float) -> float:
+        """Whole-job throughput: the units every rank processed over the
+        slowest rank's time (each rank runs an independent replica)."""
+        return self.sum(units) / self.max(seconds)
+
 
 # ----------------------------------------------------------------- clocks
 class ClockSampler:
@@ -329,6 +334,10 @@ def run_blco(args, ranks: Ranks):
     torch.cuda.synchronize()
     build_ms = eb0.elapsed_time(eb1)
     info = t.info()
+    # the same store with plain float32 run sums, for the bf16 comparison
+    t_plain = None
+    if not args.no_bf16 and not info["streamed"]:
+        t_plain = blco.Tensor.build(coords, vals, spec.dims, plain_sums=True)
     coords_h = coords[: min(spec.nnz, 1_000_000)].cpu()
     vals_h = vals[: min(spec.nnz, 1_000_000)].cpu()
     del coords, vals
@@ -340,22 +349,26 @@ def run_blco(args, ranks: Ranks):
         sv = t.values()
         grads = [torch.empty((d, R), dtype=torch.float32, device=dev) for d in spec.dims]
 
-        def make_step(factors):
+        def make_step(factors, tt=None):
+            tt = tt or t
+
             def step():
                 # the sparse CP model at the nonzeros and the adjoint of a
                 # least-squares loss for every factor (one kernel each)
-                xhat = t.cp_fwd(factors)
+                xhat = tt.cp_fwd(factors)
                 g = xhat - sv
                 for n in range(spec.order):
-                    t.cp_bwd(n, g, factors, out=grads[n])
+                    tt.cp_bwd(n, g, factors, out=grads[n])
             return step
         metric = "sparse CP forward + adjoint (all factors) throughput"
         kernel_kinds = ("mttkrp", "cp_fwd")
     else:
-        def make_step(factors):
+        def make_step(factors, tt=None):
+            tt = tt or t
+
             def step():
                 for n in range(spec.order):
-                    t.mttkrp(n, factors, out=outs[n])
+                    tt.mttkrp(n, factors, out=outs[n])
             return step
         metric = "all-mode sparse MTTKRP throughput"
         kernel_kinds = ("mttkrp",)
@@ -376,8 +389,7 @@ def run_blco(args, ranks: Ranks):
     clocks = sampler.stop()
     ms_max = ranks.max(ms)
     ms_per_step = ms_max / args.steps
-    total_nnz = ranks.sum(spec.nnz * args.steps)
-    value = total_nnz / (ms_max / 1e3)
+    value = ranks.rate(spec.nnz * args.steps, ms / 1e3)
 
     # roofline of the MTTKRP kernel: algorithmic bytes / mean launch duration
     peak, peak_src = hbm_peak()
@@ -430,15 +442,27 @@ def run_blco(args, ranks: Ranks):
         for _ in range(args.warmup):
             step16()
         blco.blco_profile_enable(t.handle, True)
-        ms16 = ranks.max(time_steps(step16, args.steps, stream))
+        ms16_local = time_steps(step16, args.steps, stream)
+        ms16 = ranks.max(ms16_local)
         blco.blco_profile_enable(t.handle, False)
         p16 = blco.blco_profile_read(t.handle)
         l16, k16 = p16.get("mttkrp", (0, 0.0))
         b16 = sum(algorithmic_bytes(spec, R, 2, n) for n in range(spec.order)) / spec.order
         ach16 = b16 / (k16 / max(l16, 1) / 1e3) / 1e9 if l16 else None
-        extra["bf16"] = {"value": total_nnz / (ms16 / 1e3), "ms_per_step": ms16 / args.steps,
+        extra["bf16"] = {"value": ranks.rate(spec.nnz * args.steps, ms16_local / 1e3), "ms_per_step": ms16 / args.steps,
                          "speedup_vs_f32": ms_max / ms16, "roofline_frac": (ach16 / peak) if ach16 else None,
+                         "run_sums": "Kahan-compensated",
                          "error_bound": 1e-2, "error_vs": "FP64 oracle on the unrounded float32 factors"}
+        if t_plain is not None:
+            stepp = make_step(A16, t_plain)
+            for _ in range(args.warmup):
+                stepp()
+            msp_local = time_steps(stepp, args.steps, stream)
+            msp = ranks.max(msp_local)
+            extra["bf16_plain_sums"] = {"value": ranks.rate(spec.nnz * args.steps, msp_local / 1e3),
+                                        "ms_per_step": msp / args.steps, "speedup_vs_f32": ms_max / msp,
+                                        "run_sums": "plain float32 (build option plain_sums)"}
+            t_plain.destroy()
         del A16
 
     # end to end through the C ABI with host buffers (MTTKRP workloads)
@@ -459,10 +483,11 @@ def run_blco(args, ranks: Ranks):
         for _ in range(K2):
             step_e2e()
         torch.cuda.synchronize()
-        sec = ranks.max((time.perf_counter() - t0) / K2)
+        sec_local = (time.perf_counter() - t0) / K2
+        sec = ranks.max(sec_local)
         h2d = sum(d * R * 4 for d in spec.dims)
         d2h = h2d
-        e2e = {"value": ranks.sum(spec.nnz) / sec, "unit": "nnz/s (all-mode)", "h2d_bytes_per_step": h2d,
+        e2e = {"value": ranks.rate(spec.nnz, sec_local), "unit": "nnz/s (all-mode)", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": sec * 1e3, "steps": K2,
                "note": "blco_mttkrp_all with pinned host factors and host results; store built once"}
 
@@ -489,6 +514,11 @@ def run_blco(args, ranks: Ranks):
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": int(launches + zl + fl),
             "build_ms": build_ms, "gen_s": gen_s,
+            "construction": {"ms": build_ms, "nnz_per_s": spec.nnz / (build_ms / 1e3),
+                             "all_mode_steps_to_amortize": build_ms / ms_per_step,
+                             "note": "blco_build from device coordinates: linearize, radix sort, block, "
+                                     "re-encode, hot-row histograms" + (", move to pinned host memory"
+                                                                        if info["streamed"] else "")},
             "store": {"nblocks": info["nblocks"], "streamed": info["streamed"], "hot_rows": info["hot_rows"],
                       "device_bytes": info["device_bytes"]}}
     line.update(extra)

@@ -74,7 +74,10 @@ typedef struct {
     int32_t n_queues;            /* streaming device queues, 1..8; 0 = 8 */
     int64_t device_budget_bytes; /* cap on this handle's device memory; 0 = none */
     int32_t force_stream;        /* 1 = keep the store in pinned host memory */
-    int32_t reserved;
+    int32_t plain_sums;          /* 1 = with bf16/fp16 factors, sum each run of
+                                    equal output rows in plain float32 instead of
+                                    Kahan's compensated sum (faster; about one
+                                    rounding per term more within a run) */
 } blco_build_opts;
 
 typedef struct {
@@ -268,6 +271,24 @@ typedef struct {
 
 blco_status blco_profile_enable(blco_handle h, int enable);
 blco_status blco_profile_read(blco_handle h, blco_profile_entry *entries, int capacity, int *count);
+
+/*
+ * Host-side fault injection, for testing callers' error paths (no
+ * counterpart in the paper). Arms the k-th next event of `kind`, counted from
+ * this call, to fail as a real failure of that kind would; k = 0 disarms.
+ * Nothing faults on the GPU: the library reports the failure and cleans up.
+ *   BLCO_FAULT_ALLOC  a device allocation of the library (store, queue
+ *                     reservations, construction scratch) -> BLCO_ERR_OOM;
+ *                     the call releases what it had allocated.
+ *   BLCO_FAULT_COPY   a batch copy of a streamed store -> BLCO_ERR_CUDA; the
+ *                     work already queued by the call is joined into the
+ *                     caller's stream, and the handle stays usable.
+ * The armed state is per process. Returns BLCO_ERR_ARG for an unknown kind
+ * or k < 0.
+ */
+typedef enum { BLCO_FAULT_ALLOC = 1, BLCO_FAULT_COPY = 2 } blco_fault_kind;
+
+blco_status blco_inject_fault(int kind, int64_t k);
 
 #ifdef __cplusplus
 }

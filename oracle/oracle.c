@@ -417,11 +417,12 @@ void orc_mttkrp(int64_t nnz, int N, const uint32_t *coords, const double *vals,
 /*
  * orc_mttkrp restricted to the output rows rows[0..nsel) (sorted ascending,
  * distinct): row rows[k] goes to Msel/Ssel row k (nsel x R, zeroed here).
- * One pass lists, per chosen row and in input order, the nonzeros that hit
- * it (a bitmap filters, a binary search finds the row); then each chosen row
- * sums its own list in input order. Rows are independent, so they may be
- * summed by several threads (OpenMP, when compiled with it): every row's sum
- * is the same sequence of additions as in a single-threaded loop.
+ * Two passes over the nonzeros list, per chosen row and in input order, the
+ * nonzeros that hit it (a bitmap filters, a binary search finds the row);
+ * then each chosen row sums its own list in input order. Chunks of the
+ * nonzeros, and the rows, are independent, so they may be handled by several
+ * threads (OpenMP, when compiled with it): every row's sum is the same
+ * sequence of additions as in a single-threaded loop.
  */
 static int64_t orc_find_row(const int64_t *rows, int64_t nsel, int64_t i) {
     int64_t a = 0, z = nsel - 1;
@@ -440,32 +441,44 @@ void orc_mttkrp_rows(int64_t nnz, int N, const uint32_t *coords, const double *v
     memset(Ssel, 0, sizeof(double) * (size_t)nsel * (size_t)R);
     if (nsel <= 0) return;
     const int64_t I = dims[mode];
+    /* The nonzeros are cut into NC consecutive chunks; chunk t's hits on row
+     * k land after those of chunks 0..t-1, so every list stays in input
+     * order whichever thread handles which chunk. */
+    enum { NC = 64 };
+    const int64_t per = (nnz + NC - 1) / NC;
     unsigned char *chosen = (unsigned char *)calloc((size_t)(I / 8 + 1), 1);
     int64_t *start = (int64_t *)calloc((size_t)nsel + 1, sizeof(int64_t));
-    if (!chosen || !start) {
-        free(chosen);
-        free(start);
-        return;
-    }
+    int64_t *at = (int64_t *)calloc((size_t)NC * (size_t)nsel, sizeof(int64_t)); /* [chunk][row] */
+    int64_t *list = NULL;
+    if (!chosen || !start || !at) goto done;
     for (int64_t k = 0; k < nsel; ++k) chosen[rows[k] >> 3] |= (unsigned char)(1u << (rows[k] & 7));
-    for (int64_t j = 0; j < nnz; ++j) {
-        const int64_t i = coords[j * N + mode];
-        if ((chosen[i >> 3] >> (i & 7)) & 1) start[orc_find_row(rows, nsel, i) + 1]++;
+#pragma omp parallel for schedule(static)
+    for (int t = 0; t < NC; ++t) {
+        const int64_t j1 = (t + 1) * per < nnz ? (t + 1) * per : nnz;
+        for (int64_t j = t * per; j < j1; ++j) {
+            const int64_t i = coords[j * N + mode];
+            if ((chosen[i >> 3] >> (i & 7)) & 1) at[(int64_t)t * nsel + orc_find_row(rows, nsel, i)]++;
+        }
     }
-    for (int64_t k = 0; k < nsel; ++k) start[k + 1] += start[k];
-    int64_t *list = (int64_t *)malloc(sizeof(int64_t) * (size_t)(start[nsel] > 0 ? start[nsel] : 1));
-    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)nsel);
-    if (!list || !fill) {
-        free(chosen);
-        free(start);
-        free(list);
-        free(fill);
-        return;
+    for (int64_t k = 0; k < nsel; ++k) {
+        int64_t pos = start[k];
+        for (int t = 0; t < NC; ++t) {
+            const int64_t c = at[(int64_t)t * nsel + k];
+            at[(int64_t)t * nsel + k] = pos;
+            pos += c;
+        }
+        start[k + 1] = pos;
     }
-    memcpy(fill, start, sizeof(int64_t) * (size_t)nsel);
-    for (int64_t j = 0; j < nnz; ++j) {
-        const int64_t i = coords[j * N + mode];
-        if ((chosen[i >> 3] >> (i & 7)) & 1) list[fill[orc_find_row(rows, nsel, i)]++] = j;
+    list = (int64_t *)malloc(sizeof(int64_t) * (size_t)(start[nsel] > 0 ? start[nsel] : 1));
+    if (!list) goto done;
+#pragma omp parallel for schedule(static)
+    for (int t = 0; t < NC; ++t) {
+        int64_t *fill = at + (int64_t)t * nsel;
+        const int64_t j1 = (t + 1) * per < nnz ? (t + 1) * per : nnz;
+        for (int64_t j = t * per; j < j1; ++j) {
+            const int64_t i = coords[j * N + mode];
+            if ((chosen[i >> 3] >> (i & 7)) & 1) list[fill[orc_find_row(rows, nsel, i)]++] = j;
+        }
     }
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t k = 0; k < nsel; ++k) {
@@ -483,10 +496,11 @@ void orc_mttkrp_rows(int64_t nnz, int N, const uint32_t *coords, const double *v
             }
         }
     }
+done:
     free(chosen);
     free(start);
+    free(at);
     free(list);
-    free(fill);
 }
 
 /* CP model value at each nonzero: xhat_j = sum_r prod_n A_n[i_n^j, r]. */

@@ -27,19 +27,20 @@ BLCO_OK, BLCO_ERR_ARG, BLCO_ERR_INDEX, BLCO_ERR_OOM, BLCO_ERR_CUDA, BLCO_ERR_TIM
 STATUS_NAMES = ["BLCO_OK", "BLCO_ERR_ARG", "BLCO_ERR_INDEX", "BLCO_ERR_OOM", "BLCO_ERR_CUDA", "BLCO_ERR_TIMEOUT",
                 "BLCO_ERR_STATE", "BLCO_ERR_UNSUPPORTED"]
 BLCO_F32, BLCO_BF16, BLCO_F16 = 0, 1, 2
+BLCO_FAULT_ALLOC, BLCO_FAULT_COPY = 1, 2
 _DTYPE_CODE = {torch.float32: BLCO_F32, torch.bfloat16: BLCO_BF16, torch.float16: BLCO_F16}
 
 # Every symbol include/blco.h declares (checked by the test suite).
 EXPORTS = ["blco_default_opts", "blco_build", "blco_mttkrp", "blco_mttkrp_all", "blco_cp_fwd", "blco_cp_bwd",
            "blco_values", "blco_perm", "blco_keys", "blco_blocks", "blco_info", "blco_sync", "blco_destroy",
            "blco_last_error", "blco_convert", "blco_gram", "blco_cpals_update", "blco_cpals_fit", "blco_norm2",
-           "blco_profile_enable", "blco_profile_read", "blco_cpals_update_noalloc"]
+           "blco_profile_enable", "blco_profile_read", "blco_cpals_update_noalloc", "blco_inject_fault"]
 
 
 class BuildOpts(ctypes.Structure):
     _fields_ = [("max_nnz_per_block", ctypes.c_int64), ("line_bits", ctypes.c_int32), ("n_queues", ctypes.c_int32),
                 ("device_budget_bytes", ctypes.c_int64), ("force_stream", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("plain_sums", ctypes.c_int32)]
 
 
 class ProfileEntry(ctypes.Structure):
@@ -91,6 +92,7 @@ def _load():
         "blco_norm2": [vp, vp, vp],
         "blco_profile_enable": [vp, i32],
         "blco_profile_read": [vp, vp, i32, vp],
+        "blco_inject_fault": [i32, i64],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -276,6 +278,12 @@ def blco_profile_enable(h, enable: bool):
     _check("blco_profile_enable", _lib.blco_profile_enable(h, 1 if enable else 0))
 
 
+def blco_inject_fault(kind: int, k: int):
+    """Arm the k-th next event of `kind` (BLCO_FAULT_ALLOC / BLCO_FAULT_COPY)
+    to fail on the host; 0 disarms."""
+    _check("blco_inject_fault", _lib.blco_inject_fault(kind, k))
+
+
 def blco_profile_read(h) -> dict:
     """{kernel kind: (launches, total_ms)} recorded since the last read."""
     cap = 16
@@ -295,7 +303,8 @@ class Tensor:
 
     @classmethod
     def build(cls, coords, vals, dims: Sequence[int], *, max_nnz_per_block: int = 0, line_bits: int = 0,
-              n_queues: int = 0, device_budget_bytes: int = 0, force_stream: bool = False, stream=None) -> "Tensor":
+              n_queues: int = 0, device_budget_bytes: int = 0, force_stream: bool = False,
+              plain_sums: bool = False, stream=None) -> "Tensor":
         o = blco_default_opts()
         if max_nnz_per_block:
             o.max_nnz_per_block = int(max_nnz_per_block)
@@ -305,6 +314,7 @@ class Tensor:
             o.n_queues = int(n_queues)
         o.device_budget_bytes = int(device_budget_bytes)
         o.force_stream = 1 if force_stream else 0
+        o.plain_sums = 1 if plain_sums else 0
         return cls(blco_build(coords, vals, dims, o, stream), dims)
 
     @property

@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libblco.so")
-SOURCES = ["api.cu", "build.cu", "mttkrp.cu", "dense.cu"]
+SOURCES = ["api.cu", "build.cu", "mttkrp.cu", "mttkrp_f32.cu", "mttkrp_bf16.cu", "mttkrp_f16.cu", "dense.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -44,7 +44,8 @@ def _stale(target: str, deps) -> bool:
 
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
-    headers = [os.path.join(CSRC, "internal.h"), os.path.join(INCLUDE, "blco.h")]
+    headers = [os.path.join(CSRC, "internal.h"), os.path.join(CSRC, "mttkrp_kernels.cuh"),
+               os.path.join(INCLUDE, "blco.h")]
     objs, jobs = [], []
     for src in SOURCES:
         s = os.path.join(CSRC, src)

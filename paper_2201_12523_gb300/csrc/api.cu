@@ -43,18 +43,15 @@ blco_status cuda_fail(cudaError_t e, const char *what) {
     return fail(e == cudaErrorMemoryAllocation ? BLCO_ERR_OOM : BLCO_ERR_CUDA, m);
 }
 
-// Fault injection for tests: BLCO_FAULT_ALLOC=k makes the k-th device
-// allocation of the library (counted from 1, per process) report failure.
-std::atomic<long> g_alloc_counter{0};
-long fault_alloc_at() {
-    const char *v = getenv("BLCO_FAULT_ALLOC");
-    return v ? atol(v) : 0;
+// Host-side fault injection (blco_inject_fault): events of a kind left
+// until the armed one fails; 0 = disarmed.
+std::atomic<long> g_fault_left[3];
+bool fault_now(int kind) {
+    long v = g_fault_left[kind].load();
+    while (v > 0)
+        if (g_fault_left[kind].compare_exchange_weak(v, v - 1)) return v == 1;
+    return false;
 }
-long fault_copy_at() {
-    const char *v = getenv("BLCO_FAULT_COPY");
-    return v ? atol(v) : 0;
-}
-std::atomic<long> g_copy_counter{0};
 
 bool is_device_ptr(const void *p) {
     if (!p) return false;
@@ -91,6 +88,7 @@ struct blco_tensor {
     int nq = 8;
     int64_t budget = 0;
     bool streamed = false;
+    bool compensated = true;  // 16-bit factors: Kahan-compensated run sums
     // store (device when resident, pinned host when streamed)
     uint64_t *d_keys = nullptr;
     float *d_vals = nullptr;
@@ -134,9 +132,7 @@ struct blco_tensor {
     std::vector<Mark> marks;
 
     cudaError_t dalloc(void **p, size_t bytes) {
-        const long at = fault_alloc_at();
-        const long k = ++g_alloc_counter;
-        if (at > 0 && k == at) return cudaErrorMemoryAllocation;
+        if (fault_now(BLCO_FAULT_ALLOC)) return cudaErrorMemoryAllocation;
         if (!building && budget > 0 && dev_bytes + (int64_t)bytes > budget) return cudaErrorMemoryAllocation;
         cudaError_t e = cudaMalloc(p, bytes ? bytes : 1);
         if (e == cudaSuccess) dev_bytes += (int64_t)bytes;
@@ -314,25 +310,34 @@ blco_status over_store(blco_tensor *h, const char *name, const float *vals_ext, 
         if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
         return BLCO_OK;
     }
+    // The copies into a queue's reservation only wait for that queue's
+    // previous kernel (stream order), so they may start while earlier work on
+    // `s` (the previous mode, the output zeroing) is still running; each
+    // queue's first kernel of this call waits for `s`. Whatever happens, every
+    // queue that received work is joined back into `s` before returning, so
+    // no work of a failed call outlives it on the queues.
     cudaError_t e = cudaEventRecord(h->ev_fork, s);
     if (e != cudaSuccess) return cuda_fail(e, "event record");
-    for (int q = 0; q < h->nq; ++q) {
-        e = cudaStreamWaitEvent(h->q_stream[q], h->ev_fork, 0);
-        if (e != cudaSuccess) return cuda_fail(e, "stream wait");
-    }
-    const long fault = fault_copy_at();
-    for (size_t b = 0; b < h->batches.size(); ++b) {
+    bool used[8] = {};
+    blco_status st = BLCO_OK;
+    for (size_t b = 0; b < h->batches.size() && st == BLCO_OK; ++b) {
         const int q = (int)(b % h->nq);
         const auto &bt = h->batches[b];
         const int64_t n = bt.end - bt.begin;
-        if (fault > 0 && ++g_copy_counter == fault)
-            return fail(BLCO_ERR_CUDA, "injected copy fault (BLCO_FAULT_COPY)");
+        if (fault_now(BLCO_FAULT_COPY)) {
+            st = fail(BLCO_ERR_CUDA, "injected host-to-device copy fault");
+            break;
+        }
         e = cudaMemcpyAsync(h->q_keys[q], h->h_keys + bt.begin, sizeof(uint64_t) * n, cudaMemcpyHostToDevice,
                             h->q_stream[q]);
         if (e == cudaSuccess && !vals_ext)
             e = cudaMemcpyAsync(h->q_vals[q], h->h_vals + bt.begin, sizeof(float) * n, cudaMemcpyHostToDevice,
                                 h->q_stream[q]);
-        if (e != cudaSuccess) return cuda_fail(e, "queue upload");
+        used[q] = true;
+        if (e != cudaSuccess) {
+            st = cuda_fail(e, "queue upload");
+            break;
+        }
         StoreView sv = h->view();
         sv.keys = h->q_keys[q];
         sv.key_origin = bt.begin;
@@ -345,15 +350,23 @@ blco_status over_store(blco_tensor *h, const char *name, const float *vals_ext, 
         }
         sv.begin = bt.begin;
         sv.end = bt.end;
+        if (b < (size_t)h->nq) {  // the queue's first kernel of this call
+            e = cudaStreamWaitEvent(h->q_stream[q], h->ev_fork, 0);
+            if (e != cudaSuccess) {
+                st = cuda_fail(e, "stream wait");
+                break;
+            }
+        }
         e = launch(sv, h->q_stream[q]);
-        if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+        if (e != cudaSuccess) st = cuda_fail(e, "kernel launch");
     }
     for (int q = 0; q < h->nq; ++q) {
+        if (!used[q]) continue;
         e = cudaEventRecord(h->q_done[q], h->q_stream[q]);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->q_done[q], 0);
-        if (e != cudaSuccess) return cuda_fail(e, "queue join");
+        if (e != cudaSuccess && st == BLCO_OK) st = cuda_fail(e, "queue join");
     }
-    return BLCO_OK;
+    return st;
 }
 
 // Rows of `mode` accumulated on chip: every row when the mode fits, else the
@@ -377,7 +390,7 @@ blco_status mttkrp_device(blco_tensor *h, int mode, const FactorSet &fs, blco_dt
     if (e != cudaSuccess) return cuda_fail(e, "zero output");
     const HotRows hot = hot_for(h, mode, R);
     return over_store(h, "mttkrp", vals_ext, s, [&](const StoreView &sv, cudaStream_t st) {
-        return launch_mttkrp(sv, fs, fdt, R, mode, hot, out, st);
+        return launch_mttkrp(sv, fs, fdt, R, mode, hot, out, h->compensated, st);
     });
 }
 
@@ -393,6 +406,13 @@ blco_status check_common(blco_tensor *h, blco_dtype fdt, int R) {
 extern "C" {
 
 const char *blco_last_error(void) { return g_err.c_str(); }
+
+blco_status blco_inject_fault(int kind, int64_t k) {
+    if (kind != BLCO_FAULT_ALLOC && kind != BLCO_FAULT_COPY) return fail(BLCO_ERR_ARG, "unknown fault kind");
+    if (k < 0) return fail(BLCO_ERR_ARG, "k must be >= 0");
+    g_fault_left[kind].store((long)k);
+    return BLCO_OK;
+}
 
 blco_status blco_default_opts(blco_build_opts *o) {
     if (!o) return fail(BLCO_ERR_ARG, "opts is NULL");
@@ -423,6 +443,7 @@ blco_status blco_build(const uint32_t *coords, const float *vals, int64_t nnz, c
         if (opts->n_queues) o.n_queues = opts->n_queues;
         o.device_budget_bytes = opts->device_budget_bytes;
         o.force_stream = opts->force_stream;
+        o.plain_sums = opts->plain_sums;
     }
     blco_tensor *h = new blco_tensor();
     h->L.N = N;
@@ -439,6 +460,7 @@ blco_status blco_build(const uint32_t *coords, const float *vals, int64_t nnz, c
     h->max_nnz = o.max_nnz_per_block;
     h->nq = o.n_queues;
     h->budget = o.device_budget_bytes;
+    h->compensated = o.plain_sums == 0;
     if (cudaGetDevice(&h->device) != cudaSuccess) {
         cudaGetLastError();
         delete h;
@@ -469,10 +491,7 @@ blco_status blco_build(const uint32_t *coords, const float *vals, int64_t nnz, c
         if (e != cudaSuccess) BAIL(cuda_fail(e, "value upload"));
         dv = tv;
     }
-    {
-        const long at = fault_alloc_at();
-        if (at > 0 && ++g_alloc_counter == at) BAIL(fail(BLCO_ERR_OOM, "injected allocation fault (BLCO_FAULT_ALLOC)"));
-    }
+    if (fault_now(BLCO_FAULT_ALLOC)) BAIL(fail(BLCO_ERR_OOM, "injected allocation fault (construction scratch)"));
     e = build_store(h->L, dc, dv, nnz, h->max_nnz, bo, s, why);
     if (e != cudaSuccess) BAIL(cuda_fail(e, "store construction"));
     if (bo.first_bad >= 0) BAIL(fail(BLCO_ERR_INDEX, why));

@@ -421,18 +421,28 @@ __global__ void k_tile_block(const int64_t *__restrict__ bstart, int64_t nblocks
 }
 
 __global__ void k_histogram(const StoreView sv, int mode, uint32_t *__restrict__ counts) {
-    for (int64_t pos = sv.begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; pos < sv.end;
-         pos += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t key = sv.keys[pos - sv.key_origin];
-        uint32_t base = 0;
-        if (!sv.single_block) {
-            uint32_t b = sv.tile_block[pos >> 5];
-            while (pos >= sv.bstart[b + 1]) ++b;
-            base = sv.bbase[(size_t)b * MAXN + mode];
+    // The loop bound is uniform over the block, so whole warps iterate
+    // together and the row match runs over an explicit mask of live lanes.
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p0 = sv.begin + (int64_t)blockIdx.x * blockDim.x; p0 < sv.end; p0 += stride) {
+        const int64_t pos = p0 + threadIdx.x;
+        const bool live = pos < sv.end;
+        uint32_t row = 0;
+        if (live) {
+            const uint64_t key = sv.keys[pos - sv.key_origin];
+            uint32_t base = 0;
+            if (!sv.single_block) {
+                uint32_t b = sv.tile_block[pos >> 5];
+                while (pos >= sv.bstart[b + 1]) ++b;
+                base = sv.bbase[(size_t)b * MAXN + mode];
+            }
+            row = (uint32_t)((key >> sv.shift[mode]) & sv.mask[mode]) + base;
         }
-        const uint32_t row = (uint32_t)((key >> sv.shift[mode]) & sv.mask[mode]) + base;
-        const unsigned peers = __match_any_sync(__activemask(), row);
-        if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&counts[row], (uint32_t)__popc(peers));
+        const unsigned lanes = __ballot_sync(0xFFFFFFFFu, live);
+        if (live) {
+            const unsigned peers = __match_any_sync(lanes, row);
+            if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&counts[row], (uint32_t)__popc(peers));
+        }
     }
 }
 

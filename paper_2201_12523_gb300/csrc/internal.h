@@ -63,11 +63,25 @@ struct HotRows {
 };
 
 // ----------------------------------------------------------------- kernels
-// mttkrp.cu
+// mttkrp.cu (dispatch by factor type). With 16-bit factors `compensated`
+// selects Kahan-compensated run sums; float32 factors always sum plainly.
 cudaError_t launch_mttkrp(const StoreView &sv, const FactorSet &fs, blco_dtype fdt, int R, int mode,
-                          const HotRows &hot, float *out, cudaStream_t s);
+                          const HotRows &hot, float *out, bool compensated, cudaStream_t s);
 cudaError_t launch_cp_fwd(const StoreView &sv, const FactorSet &fs, blco_dtype fdt, int R,
                           float *xhat, int64_t xhat_origin, cudaStream_t s);
+// mttkrp_f32.cu, mttkrp_bf16.cu, mttkrp_f16.cu (one factor type each)
+cudaError_t launch_mttkrp_f32(const StoreView &sv, const FactorSet &fs, int R, int mode, const HotRows &hot,
+                              float *out, cudaStream_t s);
+cudaError_t launch_mttkrp_bf16(const StoreView &sv, const FactorSet &fs, int R, int mode, const HotRows &hot,
+                               float *out, bool compensated, cudaStream_t s);
+cudaError_t launch_mttkrp_f16(const StoreView &sv, const FactorSet &fs, int R, int mode, const HotRows &hot,
+                              float *out, bool compensated, cudaStream_t s);
+cudaError_t launch_cp_fwd_f32(const StoreView &sv, const FactorSet &fs, int R, float *xhat, int64_t xorigin,
+                              cudaStream_t s);
+cudaError_t launch_cp_fwd_bf16(const StoreView &sv, const FactorSet &fs, int R, float *xhat, int64_t xorigin,
+                               cudaStream_t s);
+cudaError_t launch_cp_fwd_f16(const StoreView &sv, const FactorSet &fs, int R, float *xhat, int64_t xorigin,
+                              cudaStream_t s);
 bool rank_supported(int R);
 int mttkrp_hot_capacity(int R);  // max rows per launch accumulated on chip for rank R
 int warp_tier_capacity(int R);   // rows of the per-warp (read-modify-write) tier for rank R

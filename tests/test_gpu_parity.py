@@ -165,6 +165,26 @@ def test_mttkrp_16bit_factors(dtype):
     check_mttkrp_all(t, coords, vals, A16, spec.dims, tol=BF16_TOL, factors_ref=to_np64(A))
 
 
+@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])
+@pytest.mark.parametrize("R", [32, 64, 128])
+def test_16bit_run_sum_is_compensated(dtype, R):
+    """Eight nonzeros of one output row, the first 1.0 and seven of 2^-25,
+    all within one subgroup's run (factors of ones are exact in 16 bits).
+    The compensated run sum returns the float32 nearest the exact
+    1 + 1.75 * 2^-23, i.e. 1 + 2^-22; with plain_sums the terms are added one
+    by one in float32 and each tiny one is lost: 1.0."""
+    dims = (4, 8, 2)
+    c = np.array([[1, j, 0] for j in range(8)], dtype=np.int32)  # ALTO order = j order
+    v = np.array([1.0] + [2.0 ** -25] * 7, dtype=np.float32)
+    A = [blco.convert(torch.ones((d, R), device="cuda"), dtype) for d in dims]
+    for plain, want in [(False, 1.0 + 2.0 ** -22), (True, 1.0)]:
+        t = blco.Tensor.build(torch.from_numpy(c).cuda(), torch.from_numpy(v).cuda(), dims, plain_sums=plain)
+        assert np.array_equal(t.perm(), np.arange(8))
+        out = t.mttkrp(0, A).cpu().numpy()
+        assert np.all(out[1] == np.float32(want)), (plain, out[1])
+        assert np.all(out[[0, 2, 3]] == 0.0)
+
+
 def test_convert_matches_oracle_rounding():
     x = torch.randn(100_003, device="cuda") * 3
     y = blco.convert(x, torch.bfloat16)

@@ -310,11 +310,14 @@ def test_normalizer_is_mttkrp_of_absolute_values(orc):
         assert np.array_equal(S, Mabs)
 
 
-def test_mttkrp_rows_matches_full(orc):
-    rng = np.random.default_rng(10)
+@pytest.mark.parametrize("nnz", [0, 5, 2000, 4099])
+def test_mttkrp_rows_matches_full(orc, nnz):
+    # bit-identical to the full product: the chunked listing keeps every
+    # row's additions in input order, for any nnz (empty and partial chunks)
+    rng = np.random.default_rng(10 + nnz)
     dims = (40, 30, 20)
-    coords = np.stack([rng.integers(0, d, 2000) for d in dims], 1)
-    vals = rng.random(2000)
+    coords = np.stack([rng.integers(0, d, nnz) for d in dims], 1)
+    vals = rng.random(nnz)
     A = [rng.standard_normal((d, 8)) for d in dims]
     for n in range(3):
         M, S = orc.mttkrp(coords, vals, dims, A, n)
