@@ -174,8 +174,14 @@ def hbm_peak():
 
 
 def mttkrp_src_sha() -> str:
-    with open(os.path.join(ROOT, "paper_2201_12523_gb300", "csrc", "mttkrp.cu"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()
+    """sha256 over the float32 MTTKRP kernel's sources (the kernel header and
+    its translation unit), to tell whether a recorded ncu traffic figure
+    still describes the kernel being timed."""
+    h = hashlib.sha256()
+    for name in ("mttkrp_kernels.cuh", "mttkrp_f32.cu"):
+        with open(os.path.join(ROOT, "paper_2201_12523_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 def algorithmic_bytes(spec, R: int, fbytes: int, mode: int) -> int:

@@ -83,8 +83,7 @@ cudaError_t launch_cp_fwd_bf16(const StoreView &sv, const FactorSet &fs, int R, 
 cudaError_t launch_cp_fwd_f16(const StoreView &sv, const FactorSet &fs, int R, float *xhat, int64_t xorigin,
                               cudaStream_t s);
 bool rank_supported(int R);
-int mttkrp_hot_capacity(int R);  // max rows per launch accumulated on chip for rank R
-int warp_tier_capacity(int R);   // rows of the per-warp (read-modify-write) tier for rank R
+int warp_tier_capacity(int R);  // rows per launch accumulated on chip (per-warp copies) at rank R
 
 // build.cu
 struct BuildOut {

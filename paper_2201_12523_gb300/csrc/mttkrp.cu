@@ -7,7 +7,6 @@ namespace blco {
 
 bool rank_supported(int R) { return R == 8 || R == 16 || R == 32 || R == 64 || R == 128; }
 
-int mttkrp_hot_capacity(int R) { return rank_supported(R) ? warp_tier_rows(R) + cta_tier_rows(R) : 0; }
 int warp_tier_capacity(int R) { return rank_supported(R) ? warp_tier_rows(R) : 0; }
 
 cudaError_t launch_mttkrp(const StoreView &sv, const FactorSet &fs, blco_dtype fdt, int R, int mode,

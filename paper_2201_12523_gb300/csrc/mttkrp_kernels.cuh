@@ -20,15 +20,14 @@
 //      row loads of up to 8 positions back to back, multiplying with packed
 //      f32x2 arithmetic and keeping a running float32 sum while the target
 //      row stays the same (Section 5.1, computing phase);
-//   4. where a run ends the sum goes to one of three places: the warp's own
-//      shared-memory copy of the row (the mode's hottest rows, plain
-//      read-modify-write), the CTA's shared copy (the next hottest, shared
-//      atomics), or global memory with one red.global.add.v4.f32 per 16
-//      bytes (every other row: Section 5.2's register-based path). Hot rows
-//      are picked at build time from a per-mode histogram; when the whole
-//      mode fits, every row is hot. Each CTA adds its shared copies to
-//      global memory once at exit (Section 5.1's local stash and final
-//      merge; the per-mode choice of Section 5.3 becomes a per-row split).
+//   4. where a run ends the sum goes either to the warp's own shared-memory
+//      copy of the row (the mode's hottest rows, plain read-modify-write) or
+//      to global memory with one red.global.add.v4.f32 per 16 bytes (every
+//      other row: Section 5.2's register-based path). Hot rows are picked at
+//      build time from a per-mode histogram; when the whole mode fits, every
+//      row is hot. Each CTA adds its warps' copies to global memory once at
+//      exit (Section 5.1's local stash and final merge; the per-mode choice
+//      of Section 5.3 becomes a per-row split).
 // The grid is persistent (SM count x resident CTAs); warps stride over the
 // tiles, so the warps running at any moment cover a narrow window of the ALTO
 // order and share factor rows in L2.
@@ -77,12 +76,10 @@ struct KParams {
     float *out;
     int64_t out_origin;
     // on-chip accumulation of the hottest rows: the first kw rows of
-    // hot_rows in per-warp copies (warp tier), the next hc in one copy per
-    // CTA (CTA tier); with hot_dense every row of the mode is warp-tier and
-    // slot == row
+    // hot_rows get one private copy per warp; with hot_dense every row of
+    // the mode does and slot == row
     const uint32_t *hot_rows;
     int kw;
-    int hc;
     int hot_dense;
     int log2nb;  // 2^log2nb buckets of 8 hot row ids (-1: no table)
 };
@@ -260,14 +257,13 @@ __host__ __device__ constexpr int gather_slots() {
 // up to 16 bytes (the warp-tier updates and the bucket reads are 16-byte
 // vector accesses). Used by the kernel and by its launcher.
 struct SmemLayout {
-    size_t wacc, cacc, bkey, bslot, bfill, total;
+    size_t wacc, bkey, bslot, bfill, total;
 };
 __host__ __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
-__host__ __device__ __forceinline__ SmemLayout smem_layout(size_t stage_bytes, int kw, int hc, int R, int nb) {
+__host__ __device__ __forceinline__ SmemLayout smem_layout(size_t stage_bytes, int kw, int R, int nb) {
     SmemLayout L;
     L.wacc = align16(stage_bytes * kWarps);
-    L.cacc = align16(L.wacc + (size_t)kWarps * kw * R * sizeof(float));
-    L.bkey = align16(L.cacc + (size_t)hc * (R + 1) * sizeof(float));
+    L.bkey = align16(L.wacc + (size_t)kWarps * kw * R * sizeof(float));
     L.bslot = align16(L.bkey + (size_t)nb * 8 * sizeof(uint32_t));
     L.bfill = align16(L.bslot + (size_t)nb * 8 * sizeof(uint16_t));
     L.total = align16(L.bfill + (size_t)nb * sizeof(int));
@@ -300,17 +296,14 @@ __global__ void __launch_bounds__(kThreads, min_ctas<R, NG>()) k_mttkrp(const KP
     static_assert(G >= 1 && G <= 32 && (32 % G) == 0, "rank must give 1..32 lanes per row");
     constexpr int STEPS = G;     // sorted positions per subgroup (P = 32 / G subgroups)
     constexpr int CH = STEPS < 32 / VEC ? STEPS : 32 / VEC;  // positions per register batch (32 floats)
-    constexpr int RS = R + 1;    // CTA-tier row stride: rows spread over the banks
     constexpr int NS = gather_slots<NG>();
 
     extern __shared__ __align__(16) unsigned char smem[];
     const int kw = p.kw;  // warp tier: the hottest rows, one private copy per warp
-    const int hc = p.hc;  // CTA tier: the next rows, one copy per CTA
     const int nb = p.log2nb >= 0 ? (1 << p.log2nb) : 0;  // buckets of 8 row ids
-    const SmemLayout L = smem_layout(sizeof(Stage<NG>), kw, hc, R, nb);
+    const SmemLayout L = smem_layout(sizeof(Stage<NG>), kw, R, nb);
     Stage<NG> *stage = reinterpret_cast<Stage<NG> *>(smem);
     float *wacc_all = reinterpret_cast<float *>(smem + L.wacc);
-    float *cacc = reinterpret_cast<float *>(smem + L.cacc);
     uint32_t *bkey = reinterpret_cast<uint32_t *>(smem + L.bkey);
     uint16_t *bslot = reinterpret_cast<uint16_t *>(smem + L.bslot);
     int *bfill = reinterpret_cast<int *>(smem + L.bfill);
@@ -327,14 +320,13 @@ __global__ void __launch_bounds__(kThreads, min_ctas<R, NG>()) k_mttkrp(const KP
     // of 8 row ids filled in order of decreasing count by warp 0; a row that
     // finds its bucket full stays off chip (it is then simply a cold row)
     for (int i = threadIdx.x; i < kWarps * kw * R; i += kThreads) wacc_all[i] = 0.f;
-    for (int i = threadIdx.x; i < hc * RS; i += kThreads) cacc[i] = 0.f;
     for (int i = threadIdx.x; i < nb * 8; i += kThreads) bkey[i] = kNoRow;
     for (int i = threadIdx.x; i < nb; i += kThreads) bfill[i] = 0;
     __syncthreads();
     if (nb > 0 && wid == 0) {
-        for (int i0 = 0; i0 < kw + hc; i0 += 32) {
+        for (int i0 = 0; i0 < kw; i0 += 32) {
             const int i = i0 + lane;
-            const bool in = i < kw + hc;
+            const bool in = i < kw;
             const uint32_t row = in ? __ldg(p.hot_rows + i) : kNoRow;
             const uint32_t b = in ? hot_hash(row, p.log2nb) : 0xFFFFFFFFu;
             const unsigned same = __match_any_sync(kFull, b);
@@ -489,23 +481,17 @@ __global__ void __launch_bounds__(kThreads, min_ctas<R, NG>()) k_mttkrp(const KP
                     for (int h = 0; h < H; ++h) sum[h] = acc[h].value();
                     const uint32_t row = st.row[s];
                     const int sl = st.slot[s];
-                    const bool warp_tier = sl >= 0 && sl < kw;
+                    const bool warp_tier = sl >= 0;
                     // continuation parts at the last step: atomics first
                     const bool cont = last && !run_end && warp_tier;
                     if (row != kNoRow && !warp_tier) {
                         float sv[VEC];
 #pragma unroll
                         for (int h = 0; h < H; ++h) unpack2(sum[h], sv[2 * h], sv[2 * h + 1]);
-                        if (sl >= 0) {
-                            float *a = cacc + (size_t)(sl - kw) * RS + c * VEC;
+                        float *o2 = p.out + (size_t)row * R + c * VEC;
 #pragma unroll
-                            for (int e = 0; e < VEC; ++e) atomicAdd(a + e, sv[e]);
-                        } else {
-                            float *o2 = p.out + (size_t)row * R + c * VEC;
-#pragma unroll
-                            for (int e = 0; e < VEC; e += 4)
-                                red_add_v4(o2 + e, sv[e], sv[e + 1], sv[e + 2], sv[e + 3]);
-                        }
+                        for (int e = 0; e < VEC; e += 4)
+                            red_add_v4(o2 + e, sv[e], sv[e + 1], sv[e + 2], sv[e + 3]);
                     } else if (cont) {
                         float sv[VEC];
 #pragma unroll
@@ -553,13 +539,6 @@ __global__ void __launch_bounds__(kThreads, min_ctas<R, NG>()) k_mttkrp(const KP
         const uint32_t row = p.hot_dense ? (uint32_t)sl : __ldg(p.hot_rows + sl);
         if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f)
             red_add_v4(p.out + (size_t)row * R + q * 4, v.x, v.y, v.z, v.w);
-    }
-    for (int i = threadIdx.x; i < hc * Q; i += kThreads) {
-        const int sl = i / Q, q = i % Q;
-        const float *a = cacc + (size_t)sl * RS + q * 4;
-        const float x0 = a[0], x1 = a[1], x2 = a[2], x3 = a[3];
-        const uint32_t row = __ldg(p.hot_rows + kw + sl);
-        if (x0 != 0.f || x1 != 0.f || x2 != 0.f || x3 != 0.f) red_add_v4(p.out + (size_t)row * R + q * 4, x0, x1, x2, x3);
     }
 }
 
@@ -644,13 +623,14 @@ __global__ void __launch_bounds__(kThreads, min_ctas<R, NG>()) k_cp_fwd(const KP
 // -------------------------------------------------------------------------
 // launch helpers
 // -------------------------------------------------------------------------
-// Shared memory for on-chip accumulation, per CTA: the warp tier (kWarps
-// private copies of kw rows) and the CTA tier (hc rows, atomics).
+// Shared memory for on-chip accumulation: kWarps private copies of kw rows
+// per CTA. Measured on GB300, a second tier of rows shared by the CTA's warps
+// (shared-memory atomics) was slower than sending those rows to global
+// memory, and more rows per warp take L1 capacity from the factor-row
+// gathers: 4 KB per warp is the measured optimum at R = 16..64.
 constexpr int kWarpTierBytes = 4 * 1024;  // per warp
-constexpr int kCtaTierBytes = 24 * 1024;
 
 int warp_tier_rows(int R) { return kWarpTierBytes / (R * (int)sizeof(float)); }
-int cta_tier_rows(int R) { return kCtaTierBytes / ((R + 1) * (int)sizeof(float)); }
 
 KParams make_params(const StoreView &sv) {
     KParams p;
@@ -684,7 +664,7 @@ int grid_for(const void *kern, size_t shm, int64_t span) {
 template <typename T, int R, int NG, bool COMP>
 cudaError_t run_mttkrp_impl(const KParams &p, cudaStream_t s) {
     const int nb = p.log2nb >= 0 ? (1 << p.log2nb) : 0;
-    const size_t shm = smem_layout(sizeof(Stage<NG>), p.kw, p.hc, R, nb).total;
+    const size_t shm = smem_layout(sizeof(Stage<NG>), p.kw, R, nb).total;
     auto kern = k_mttkrp<T, R, NG, COMP>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
     if (e != cudaSuccess) return e;
@@ -771,16 +751,16 @@ cudaError_t mttkrp_as(const StoreView &sv, const FactorSet &fs, int R, int mode,
     } else if (hot.count > 0) {
         p.hot_rows = hot.rows;
         p.kw = hot.count < warp_tier_rows(R) ? hot.count : warp_tier_rows(R);
-        const int rest = hot.count - p.kw;
-        p.hc = rest < cta_tier_rows(R) ? rest : cta_tier_rows(R);
         // buckets of 8 at an average load of at most 4 rows
         int l = 0;
-        while ((1 << l) * 4 < p.kw + p.hc) ++l;
+        while ((1 << l) * 4 < p.kw) ++l;
         p.log2nb = l;
     }
     // float32 factors: plain run sums only; 16-bit factors: compensated
     // unless the caller asked for plain sums
-    if (sizeof(T) == 2 && compensated) return by_rank_mttkrp<T, true>(p, R, s);
+    if constexpr (sizeof(T) == 2) {
+        if (compensated) return by_rank_mttkrp<T, true>(p, R, s);
+    }
     return by_rank_mttkrp<T, false>(p, R, s);
 }
 
