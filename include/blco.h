@@ -126,9 +126,13 @@ blco_status blco_build(const uint32_t *coords, const float *vals, int64_t nnz, c
  *            factors[mode] is not read and may be NULL
  *   R        rank: 8, 16, 32, 64 or 128
  *   out      I_mode x R float32 (host or device); overwritten
- * Accumulation is float32 (segmented within a warp, then on-chip per CTA for
- * the handle's hot rows, then vector reductions to global memory), so the
- * summation order, and the last bits, vary from run to run.
+ * Accumulation is float32 (segmented within a warp, then in per-warp
+ * shared-memory copies of the mode's hottest rows, then vector reductions to
+ * global memory), so the summation order, and the last bits, vary from run
+ * to run. With bf16/fp16 factors each in-warp run is Kahan-compensated unless
+ * the handle was built with plain_sums.
+ * With any host pointer the call returns when `out` is complete; with device
+ * pointers only it is asynchronous on `stream`.
  * Errors: BLCO_ERR_ARG, BLCO_ERR_UNSUPPORTED (rank), BLCO_ERR_OOM (staging),
  * BLCO_ERR_CUDA.
  */
@@ -138,8 +142,12 @@ blco_status blco_mttkrp(blco_handle h, int mode, const void *const *factors, blc
 /*
  * All-mode MTTKRP with one set of factors: outs[n] = mode-n MTTKRP for every
  * n with outs[n] != NULL (Eq. 1 for each mode, as the paper's all-mode
- * measurements do). Same arguments and errors as blco_mttkrp; host factor
- * matrices are staged to the device once for all modes.
+ * measurements do). Same arguments and errors as blco_mttkrp. Host factor
+ * matrices are uploaded once for all modes, on a copy stream of the handle,
+ * in the order the modes need them; each mode's kernel waits only for the
+ * factors it gathers, and each host result is downloaded on a second copy
+ * stream while the next mode runs. The call returns when the host results
+ * are complete.
  */
 blco_status blco_mttkrp_all(blco_handle h, const void *const *factors, blco_dtype fdt, int R,
                             float *const *outs, blco_stream stream);

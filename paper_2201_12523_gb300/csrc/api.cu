@@ -31,7 +31,6 @@ int sm_count() {
 namespace {
 
 constexpr int64_t kDefaultCap = (int64_t)1 << 27;
-constexpr int kHotMax = 4096;  // rows kept per mode; a launch uses the first cap(R)
 
 blco_status fail(blco_status st, const std::string &msg) {
     g_err = msg;
@@ -120,6 +119,11 @@ struct blco_tensor {
     // staging workspace for host arguments
     void *ws = nullptr;
     size_t ws_bytes = 0;
+    // host-argument copies of blco_mttkrp_all (created on first use): uploads
+    // and downloads on their own streams, so they overlap other modes' kernels
+    cudaStream_t up = nullptr, down = nullptr;
+    cudaEvent_t ev_call = nullptr, ev_down = nullptr;
+    cudaEvent_t ev_up[MAXN] = {}, ev_out[MAXN] = {};
     int64_t dev_bytes = 0;
     int64_t host_bytes = 0;
     bool building = false;  // construction: the budget is checked once at the end
@@ -198,6 +202,14 @@ void release(blco_tensor *h) {
         if (h->q_done[q]) cudaEventDestroy(h->q_done[q]);
     }
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->up) cudaStreamDestroy(h->up);
+    if (h->down) cudaStreamDestroy(h->down);
+    for (cudaEvent_t ev : {h->ev_call, h->ev_down})
+        if (ev) cudaEventDestroy(ev);
+    for (int n = 0; n < MAXN; ++n) {
+        if (h->ev_up[n]) cudaEventDestroy(h->ev_up[n]);
+        if (h->ev_out[n]) cudaEventDestroy(h->ev_out[n]);
+    }
     for (auto &m : h->marks) {
         cudaEventDestroy(m.a);
         cudaEventDestroy(m.b);
@@ -532,7 +544,8 @@ blco_status blco_build(const uint32_t *coords, const float *vals, int64_t nnz, c
         uint32_t *counts = nullptr;
         for (int n = 0; n < N && e == cudaSuccess; ++n) {
             const int64_t I = h->L.dims[n];
-            const int k = (int)std::min<int64_t>(I, kHotMax);
+            // as many rows as the smallest supported rank can hold on chip
+            const int k = (int)std::min<int64_t>(I, warp_tier_capacity(8));
             e = cudaMallocAsync(&counts, sizeof(uint32_t) * I, s);
             if (e == cudaSuccess) e = cudaMemsetAsync(counts, 0, sizeof(uint32_t) * I, s);
             if (e == cudaSuccess) e = mode_histogram(h->view(), n, counts, s);
@@ -653,6 +666,20 @@ blco_status blco_mttkrp(blco_handle h, int mode, const void *const *factors, blc
     return BLCO_OK;
 }
 
+// Streams and events of the pipelined host-argument path.
+cudaError_t copy_streams(blco_tensor *h) {
+    if (h->up) return cudaSuccess;
+    cudaError_t e = cudaStreamCreateWithFlags(&h->up, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->down, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_call, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_down, cudaEventDisableTiming);
+    for (int n = 0; n < MAXN && e == cudaSuccess; ++n) {
+        e = cudaEventCreateWithFlags(&h->ev_up[n], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_out[n], cudaEventDisableTiming);
+    }
+    return e;
+}
+
 blco_status blco_mttkrp_all(blco_handle h, const void *const *factors, blco_dtype fdt, int R, float *const *outs,
                             blco_stream stream) {
     g_err.clear();
@@ -665,40 +692,92 @@ blco_status blco_mttkrp_all(blco_handle h, const void *const *factors, blco_dtyp
         if (outs[n] && (reinterpret_cast<uintptr_t>(outs[n]) & 15)) return fail(BLCO_ERR_ARG, "outs[n] is not 16-byte aligned");
     DeviceGuard g(h->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    bool host_out[MAXN] = {};
-    size_t extra = 0;
-    for (int n = 0; n < h->L.N; ++n) {
-        if (outs[n] && !is_device_ptr(outs[n])) {
-            host_out[n] = true;
-            extra += ((size_t)h->L.dims[n] * R * 4 + 255) / 256 * 256;
+    const int N = h->L.N;
+    bool host_in[MAXN] = {}, host_out[MAXN] = {};
+    size_t in_off[MAXN] = {}, out_off[MAXN] = {}, total = 0;
+    auto round256 = [](size_t b) { return (b + 255) / 256 * 256; };
+    for (int k = 0; k < N; ++k) {
+        host_in[k] = !is_device_ptr(factors[k]);
+        if (host_in[k]) {
+            in_off[k] = total;
+            total += round256((size_t)h->L.dims[k] * R * dtype_size(fdt));
         }
     }
-    Staged sf;
-    void *dout = nullptr;
-    st = stage_factors(h, factors, -1, fdt, R, extra, sf, &dout, s);
-    if (st != BLCO_OK) return st;
-    size_t off = 0;
-    for (int n = 0; n < h->L.N; ++n) {
+    for (int n = 0; n < N; ++n) {
+        host_out[n] = outs[n] && !is_device_ptr(outs[n]);
+        if (host_out[n]) {
+            out_off[n] = total;
+            total += round256((size_t)h->L.dims[n] * R * sizeof(float));
+        }
+    }
+    FactorSet fs;
+    for (int k = 0; k < MAXN; ++k) fs.ptr[k] = k < N ? factors[k] : nullptr;
+    if (total == 0) {  // device arguments: the modes one after another on s
+        for (int n = 0; n < N; ++n) {
+            if (!outs[n]) continue;
+            st = mttkrp_device(h, n, fs, fdt, R, outs[n], nullptr, s);
+            if (st != BLCO_OK) return st;
+        }
+        return BLCO_OK;
+    }
+    // Host arguments. Uploads run on h->up in the order the modes need them
+    // (modes 1..N-1 first: mode 0's kernel overlaps the upload of factor 0);
+    // each mode waits only for the factors it gathers; each host result is
+    // downloaded on h->down as soon as its mode is done, overlapping the next
+    // mode. The call joins both copy streams into s and returns when the host
+    // results are complete.
+    void *p = nullptr;
+    cudaError_t e = h->workspace(total, &p);
+    if (e != cudaSuccess) return cuda_fail(e, "staging workspace");
+    char *base = static_cast<char *>(p);
+    e = copy_streams(h);
+    if (e != cudaSuccess) return cuda_fail(e, "copy streams");
+    e = cudaEventRecord(h->ev_call, s);  // earlier work on s may still use the workspace
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->up, h->ev_call, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->down, h->ev_call, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "copy streams");
+    bool uploaded = false, downloaded = false;
+    for (int i = 0; i < N && st == BLCO_OK; ++i) {
+        const int k = (i + 1) % N;
+        if (!host_in[k]) continue;
+        e = cudaMemcpyAsync(base + in_off[k], factors[k], (size_t)h->L.dims[k] * R * dtype_size(fdt),
+                            cudaMemcpyHostToDevice, h->up);
+        if (e == cudaSuccess) e = cudaEventRecord(h->ev_up[k], h->up);
+        if (e != cudaSuccess) st = cuda_fail(e, "factor upload");
+        fs.ptr[k] = base + in_off[k];
+        uploaded = true;
+    }
+    bool waited[MAXN] = {};
+    for (int n = 0; n < N && st == BLCO_OK; ++n) {
         if (!outs[n]) continue;
-        float *o = outs[n];
-        if (host_out[n]) {
-            o = reinterpret_cast<float *>(static_cast<char *>(dout) + off);
-            off += ((size_t)h->L.dims[n] * R * 4 + 255) / 256 * 256;
+        for (int k = 0; k < N && st == BLCO_OK; ++k) {
+            if (k == n || !host_in[k] || waited[k]) continue;
+            e = cudaStreamWaitEvent(s, h->ev_up[k], 0);
+            if (e != cudaSuccess) st = cuda_fail(e, "stream wait");
+            waited[k] = true;
         }
-        st = mttkrp_device(h, n, sf.fs, fdt, R, o, nullptr, s);
-        if (st != BLCO_OK) return st;
-        if (host_out[n]) {
-            cudaError_t e = cudaMemcpyAsync(outs[n], o, (size_t)h->L.dims[n] * R * 4, cudaMemcpyDeviceToHost, s);
-            if (e != cudaSuccess) return cuda_fail(e, "result download");
-        }
+        if (st != BLCO_OK) break;
+        float *o = host_out[n] ? reinterpret_cast<float *>(base + out_off[n]) : outs[n];
+        st = mttkrp_device(h, n, fs, fdt, R, o, nullptr, s);
+        if (st != BLCO_OK || !host_out[n]) continue;
+        e = cudaEventRecord(h->ev_out[n], s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->down, h->ev_out[n], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(outs[n], o, (size_t)h->L.dims[n] * R * sizeof(float), cudaMemcpyDeviceToHost, h->down);
+        if (e != cudaSuccess) st = cuda_fail(e, "result download");
+        downloaded = true;
     }
-    if (sf.used > 0) {
-        cudaError_t e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) return cuda_fail(e, "mttkrp_all");
+    // join the copy streams into s (also after an error: nothing of this call
+    // may outlive it on the copy streams)
+    for (cudaStream_t cs : {h->up, h->down}) {
+        if ((cs == h->up && !uploaded) || (cs == h->down && !downloaded)) continue;
+        e = cudaEventRecord(h->ev_down, cs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_down, 0);
+        if (e != cudaSuccess && st == BLCO_OK) st = cuda_fail(e, "copy join");
     }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "mttkrp_all");
-    return BLCO_OK;
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess && st == BLCO_OK) st = cuda_fail(e, "mttkrp_all");
+    return st;
 }
 
 blco_status blco_cp_fwd(blco_handle h, const void *const *factors, blco_dtype fdt, int R, float *xhat,

@@ -227,6 +227,32 @@ def test_host_factor_and_output_pointers():
         assert oracle.max_rel_err(outs[n], M, S) <= FP32_TOL
 
 
+@pytest.mark.parametrize("streamed", [False, True])
+def test_mttkrp_all_mixed_host_and_device_arguments(streamed):
+    """Pipelined host path: host and device factors mixed, host, device and
+    absent outputs, a resident and a streamed store; called twice in a row
+    (the staging workspace and copy streams are reused)."""
+    spec = synth.small(2, 120_000, (1 << 13, 1 << 11, 1 << 9, 1 << 7))
+    coords, vals, A = make(spec)
+    kw = dict(force_stream=True, max_nnz_per_block=5000, n_queues=3) if streamed else {}
+    t = blco.Tensor.build(coords, vals, spec.dims, **kw)
+    R = spec.rank
+    c = coords.cpu().numpy()
+    v = vals.cpu().numpy().astype(np.float64)
+    ref = [oracle.mttkrp(c, v, spec.dims, to_np64(A), n) for n in range(4)]
+    for rep in range(2):
+        facs = [A[0].cpu().numpy(), A[1], A[2].cpu().numpy(), A[3]] if rep == 0 else \
+               [A[0], A[1].cpu().numpy(), A[2], A[3].cpu().numpy()]
+        outs = [np.empty((spec.dims[0], R), np.float32), torch.empty((spec.dims[1], R), device="cuda"),
+                None, np.empty((spec.dims[3], R), np.float32)]
+        blco.blco_mttkrp_all(t.handle, facs, blco.BLCO_F32, R, outs)
+        torch.cuda.synchronize()
+        for n in (0, 1, 3):
+            got = outs[n].cpu().numpy() if isinstance(outs[n], torch.Tensor) else outs[n]
+            M, S = ref[n]
+            assert oracle.max_rel_err(got, M, S) <= FP32_TOL, (rep, n)
+
+
 def test_argument_errors():
     spec = synth.small(0, 1000, (10, 20, 30))
     coords, vals, A = make(spec)
