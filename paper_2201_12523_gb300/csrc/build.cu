@@ -420,12 +420,18 @@ __global__ void k_tile_block(const int64_t *__restrict__ bstart, int64_t nblocks
     }
 }
 
-__global__ void k_histogram(const StoreView sv, int mode, uint32_t *__restrict__ counts) {
-    // The loop bound is uniform over the block, so whole warps iterate
-    // together and the row match runs over an explicit mask of live lanes.
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t p0 = sv.begin + (int64_t)blockIdx.x * blockDim.x; p0 < sv.end; p0 += stride) {
-        const int64_t pos = p0 + threadIdx.x;
+// Row counts of one mode over a systematic sample of the store: every
+// `stride`-th 32-nonzero tile (all tiles when stride is 1), one warp per
+// sampled tile. The counts only rank rows for on-chip accumulation, so a
+// sample of tens of millions of nonzeros is enough to find the heavy rows.
+__global__ void k_histogram(const StoreView sv, int mode, int64_t stride, uint32_t *__restrict__ counts) {
+    const int64_t ntiles = (sv.end - sv.begin + 31) >> 5;
+    const int64_t nsamp = (ntiles + stride - 1) / stride;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    // the loop bound is uniform over the warp, so whole warps iterate together
+    for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < nsamp; j += nwarps) {
+        const int64_t pos = sv.begin + j * stride * 32 + lane;
         const bool live = pos < sv.end;
         uint32_t row = 0;
         if (live) {
@@ -441,7 +447,7 @@ __global__ void k_histogram(const StoreView sv, int mode, uint32_t *__restrict__
         const unsigned lanes = __ballot_sync(0xFFFFFFFFu, live);
         if (live) {
             const unsigned peers = __match_any_sync(lanes, row);
-            if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&counts[row], (uint32_t)__popc(peers));
+            if (lane == __ffs(peers) - 1) atomicAdd(&counts[row], (uint32_t)__popc(peers));
         }
     }
 }
@@ -611,7 +617,10 @@ cudaError_t build_tile_block(const int64_t *d_bstart, int64_t nblocks, int64_t n
 
 cudaError_t mode_histogram(const StoreView &sv, int mode, uint32_t *counts, cudaStream_t s) {
     if (sv.end <= sv.begin) return cudaSuccess;
-    k_histogram<<<grid_for(sv.end - sv.begin, 256), 256, 0, s>>>(sv, mode, counts);
+    const int64_t ntiles = (sv.end - sv.begin + 31) / 32;
+    const int64_t stride = std::max<int64_t>(1, ntiles >> 20);  // at most ~2^20 sampled tiles
+    const int64_t nsamp = (ntiles + stride - 1) / stride;
+    k_histogram<<<grid_for(nsamp * 32, 256), 256, 0, s>>>(sv, mode, stride, counts);
     return cudaGetLastError();
 }
 

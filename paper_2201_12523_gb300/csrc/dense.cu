@@ -5,6 +5,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "internal.h"
@@ -49,30 +50,120 @@ __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return _
 template <>
 __device__ __forceinline__ float to_f<__half>(__half v) { return __half2float(v); }
 
-// G += A^T A over a chunk of rows per CTA. Products of two float32 values are
-// exact in float64; sums run in float64 and CTA partials meet in float64
-// atomics. blockIdx.y picks a group of 256 (r, s) pairs, one per thread.
-constexpr int kGramRows = 32;
+// G = A^T A. Each thread owns a 4 x 4 block of G in the upper triangle
+// (diagonal blocks included) and accumulates its 16 dot products over its
+// CTA's rows with Ogita, Rump and Oishi's Dot2 (SIAM J. Sci. Comput. 26(6),
+// 2005): TwoProduct by FMA gives each float32 product exactly as p + e, and
+// TwoSum carries the rounding error of every addition, so each partial is a
+// float32 pair as accurate as a sum in twice the float32 precision. The pair
+// is added in float64 (hi + lo), the CTA's thread groups are summed in
+// shared memory in float64, and CTAs meet in float64 atomics (both halves of
+// an off-diagonal block). This keeps the FP64 pipe, which is a small fraction
+// of the FP32 rate on this GPU, off the O(I R^2) part of the work.
+constexpr int kGramRows = 32;  // rows staged in shared memory per step
+constexpr int kGramThreads = 256;
+
+struct GramShape {
+    int R4;      // R rounded up to 4 (padding columns are zero)
+    int B;       // 4 x 4 blocks per side
+    int nblk;    // blocks in the upper triangle
+    int groups;  // thread groups per CTA that split the rows (nblk < 256)
+};
+
+__host__ __device__ inline GramShape gram_shape(int R) {
+    GramShape g;
+    g.R4 = (R + 3) & ~3;
+    g.B = g.R4 / 4;
+    g.nblk = g.B * (g.B + 1) / 2;
+    g.groups = g.nblk >= kGramThreads ? 1 : kGramThreads / g.nblk;
+    return g;
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float z = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_gram(const T *__restrict__ A, int64_t I, int R, int64_t rows_per_cta,
-                                              double *__restrict__ G) {
+__global__ void __launch_bounds__(kGramThreads) k_gram(const T *__restrict__ A, int64_t I, int R, int64_t rows_per_cta,
+                                                       double *__restrict__ G) {
     extern __shared__ __align__(16) unsigned char smem[];
-    float *tile = reinterpret_cast<float *>(smem);  // kGramRows x R
-    const int pairs = R * R;
-    const int p = blockIdx.y * 256 + threadIdx.x;
-    const int r = p / R, c = p % R;
+    const GramShape sh = gram_shape(R);
+    float *tile = reinterpret_cast<float *>(smem);                       // kGramRows x R4
+    double *red = reinterpret_cast<double *>(tile + kGramRows * sh.R4);  // groups x nblk x 16
+    const int tid = threadIdx.x;
+    int blk, grp;
+    if (sh.groups > 1) {
+        blk = tid % sh.nblk;
+        grp = tid / sh.nblk;
+    } else {
+        blk = blockIdx.y * kGramThreads + tid;
+        grp = 0;
+    }
+    const bool active = blk < sh.nblk && grp < sh.groups;
+    int br = 0, rem = active ? blk : 0;  // upper-triangle block -> (br, bc)
+    while (rem >= sh.B - br) {
+        rem -= sh.B - br;
+        ++br;
+    }
+    const int bc = br + rem;
+    float hi[16], lo[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) hi[k] = lo[k] = 0.f;
     const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta;
     const int64_t r1 = r0 + rows_per_cta < I ? r0 + rows_per_cta : I;
-    double acc = 0.0;
-    for (int64_t b = r0; b < r1; b += kGramRows) {
-        const int nr = (int)((r1 - b) < kGramRows ? (r1 - b) : kGramRows);
+    for (int64_t b0 = r0; b0 < r1; b0 += kGramRows) {
+        const int nr = (int)((r1 - b0) < kGramRows ? (r1 - b0) : kGramRows);
         __syncthreads();
-        for (int i = threadIdx.x; i < nr * R; i += 256) tile[i] = to_f<T>(A[b * R + i]);
+        for (int i = tid; i < kGramRows * sh.R4; i += kGramThreads) {
+            const int row = i / sh.R4, col = i % sh.R4;
+            tile[i] = (row < nr && col < R) ? to_f<T>(A[(b0 + row) * R + col]) : 0.f;
+        }
         __syncthreads();
-        if (p < pairs)
-            for (int i = 0; i < nr; ++i) acc += (double)tile[i * R + r] * (double)tile[i * R + c];
+        if (!active) continue;
+        for (int i = grp; i < nr; i += sh.groups) {
+            const float4 x = *reinterpret_cast<const float4 *>(tile + i * sh.R4 + br * 4);
+            const float4 y = *reinterpret_cast<const float4 *>(tile + i * sh.R4 + bc * 4);
+            const float xa[4] = {x.x, x.y, x.z, x.w}, ya[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const float p = __fmul_rn(xa[u], ya[v]);
+                    const float e = __fmaf_rn(xa[u], ya[v], -p);  // x*y == p + e exactly
+                    float sum, err;
+                    two_sum(hi[u * 4 + v], p, sum, err);
+                    hi[u * 4 + v] = sum;
+                    lo[u * 4 + v] = __fadd_rn(lo[u * 4 + v], __fadd_rn(err, e));
+                }
+        }
     }
-    if (p < pairs) atomicAdd(&G[p], acc);
+    // sum the thread groups of this CTA in float64, then one atomic per
+    // entry. Shared slots are indexed by the block's local index: with thread
+    // groups the block itself, else the thread (blockIdx.y picks the range).
+    const int nloc = sh.groups > 1 ? sh.nblk : kGramThreads;  // local blocks per group
+    const int lbl = sh.groups > 1 ? blk : tid;
+    if (active)
+#pragma unroll
+        for (int k = 0; k < 16; ++k) red[(grp * nloc + lbl) * 16 + k] = (double)hi[k] + (double)lo[k];
+    __syncthreads();
+    const int nact = sh.groups > 1 ? sh.nblk : min(kGramThreads, sh.nblk - (int)blockIdx.y * kGramThreads);
+    for (int i = tid; i < nact * 16; i += kGramThreads) {
+        const int lb = i / 16, k = i % 16;
+        double v = 0.0;
+        for (int g2 = 0; g2 < sh.groups; ++g2) v += red[(g2 * nloc + lb) * 16 + k];
+        const int gb = sh.groups > 1 ? lb : (int)blockIdx.y * kGramThreads + lb;
+        int rr = 0, rm = gb;
+        while (rm >= sh.B - rr) {
+            rm -= sh.B - rr;
+            ++rr;
+        }
+        const int r = rr * 4 + k / 4, c = (rr + rm) * 4 + k % 4;
+        if (r >= R || c >= R) continue;
+        atomicAdd(&G[(size_t)r * R + c], v);
+        if (rr != rr + rm) atomicAdd(&G[(size_t)c * R + r], v);
+    }
 }
 
 __global__ void k_zero_d(double *p, int n) {
@@ -362,19 +453,35 @@ cudaError_t launch_gram(const void *A, blco_dtype fdt, int64_t I, int R, double 
     k_zero_d<<<1, 256, 0, s>>>(G, R * R);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || I <= 0) return e;
-    const int64_t ctas_max = (int64_t)sm_count() * 4;
+    const GramShape sh = gram_shape(R);
+    const int ny = sh.groups > 1 ? 1 : (sh.nblk + kGramThreads - 1) / kGramThreads;
+    // about two CTAs per SM in total, each over a contiguous range of rows
+    const int64_t ctas_max = std::max<int64_t>(1, (int64_t)sm_count() * 2 / ny);
     int64_t rows = (I + ctas_max - 1) / ctas_max;
-    if (rows < kGramRows) rows = kGramRows;
+    rows = std::max<int64_t>(kGramRows, (rows + kGramRows - 1) / kGramRows * kGramRows);
     const int64_t ctas = (I + rows - 1) / rows;
-    const size_t shm = sizeof(float) * kGramRows * R;
-    const dim3 grid((unsigned)ctas, (unsigned)((R * R + 255) / 256));
+    const size_t red_entries = (size_t)(sh.groups > 1 ? sh.groups * sh.nblk : kGramThreads) * 16;
+    const size_t shm = sizeof(float) * kGramRows * sh.R4 + sizeof(double) * red_entries;
+    const dim3 grid((unsigned)ctas, (unsigned)ny);
     switch (fdt) {
-        case BLCO_F32: k_gram<float><<<grid, 256, shm, s>>>(static_cast<const float *>(A), I, R, rows, G); break;
-        case BLCO_BF16:
-            k_gram<__nv_bfloat16><<<grid, 256, shm, s>>>(static_cast<const __nv_bfloat16 *>(A), I, R, rows, G);
+        case BLCO_F32:
+            e = cudaFuncSetAttribute(k_gram<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+            if (e == cudaSuccess)
+                k_gram<float><<<grid, kGramThreads, shm, s>>>(static_cast<const float *>(A), I, R, rows, G);
             break;
-        case BLCO_F16: k_gram<__half><<<grid, 256, shm, s>>>(static_cast<const __half *>(A), I, R, rows, G); break;
+        case BLCO_BF16:
+            e = cudaFuncSetAttribute(k_gram<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+            if (e == cudaSuccess)
+                k_gram<__nv_bfloat16><<<grid, kGramThreads, shm, s>>>(static_cast<const __nv_bfloat16 *>(A), I, R,
+                                                                        rows, G);
+            break;
+        case BLCO_F16:
+            e = cudaFuncSetAttribute(k_gram<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+            if (e == cudaSuccess)
+                k_gram<__half><<<grid, kGramThreads, shm, s>>>(static_cast<const __half *>(A), I, R, rows, G);
+            break;
     }
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

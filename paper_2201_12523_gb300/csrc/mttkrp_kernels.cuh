@@ -368,28 +368,33 @@ __global__ void __launch_bounds__(kThreads, min_ctas<R, NG>()) k_mttkrp(const KP
             }
         }
 
+        // Lanes past the end of the store (the ragged last tile) take lane 0's
+        // nonzero with value 0: they join its run and add exact zeros (for
+        // finite factors), so no later step needs a per-lane validity test.
+        {
+            const uint64_t key0 = __shfl_sync(kFull, key, 0);
+            if (!valid) {
+                key = key0;
+                val = 0.f;
+            }
+        }
         // --- de-linearize the target row and the gathered rows
         uint32_t t = (uint32_t)((key >> p.t_shift) & p.t_mask);
         uint32_t o[NS];
 #pragma unroll
         for (int q = 0; q < NS; ++q)
             o[q] = (q < ng) ? (uint32_t)((key >> p.gat[q].shift) & p.gat[q].mask) : 0u;
-        if (!p.single_block && valid) {
-            const uint32_t *bb = p.bbase + (size_t)block_of(p, pos) * MAXN;
+        if (!p.single_block) {
+            const uint32_t *bb = p.bbase + (size_t)block_of(p, valid ? pos : p.begin + tile * 32) * MAXN;
             t += __ldg(bb + p.t_mode);
 #pragma unroll
             for (int q = 0; q < NS; ++q)
                 if (q < ng) o[q] += __ldg(bb + p.gat[q].mode);
         }
-        if (!valid) {
-            t = kNoRow;
-#pragma unroll
-            for (int q = 0; q < NS; ++q) o[q] = 0u;
-        }
         // --- on-chip slot of this lane's row (one lookup per nonzero: two
         // 16-byte shared loads of the row's bucket, no probing loop)
         int slot = -1;
-        if (valid) {
+        {
             if (p.hot_dense) {
                 slot = (int)t;
             } else if (nb > 0) {
@@ -484,7 +489,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<R, NG>()) k_mttkrp(const KP
                     const bool warp_tier = sl >= 0;
                     // continuation parts at the last step: atomics first
                     const bool cont = last && !run_end && warp_tier;
-                    if (row != kNoRow && !warp_tier) {
+                    if (!warp_tier) {
                         float sv[VEC];
 #pragma unroll
                         for (int h = 0; h < H; ++h) unpack2(sum[h], sv[2 * h], sv[2 * h + 1]);

@@ -185,6 +185,35 @@ def test_16bit_run_sum_is_compensated(dtype, R):
         assert np.all(out[[0, 2, 3]] == 0.0)
 
 
+@pytest.mark.parametrize("nnz", [1, 31, 33, 1000, 4099])
+def test_unreferenced_nonfinite_factor_rows_do_not_leak(nnz):
+    """Ragged tails: lanes past the end of the store must not touch factor
+    rows that no nonzero references. Every unreferenced row holds Inf or NaN;
+    the outputs must still match the oracle (which never reads those rows)."""
+    rng = np.random.default_rng(nnz)
+    dims = (50, 40, 30)
+    c = np.unique(np.stack([rng.integers(1, d, nnz) for d in dims], 1), axis=0)  # row 0 never used
+    rng.shuffle(c)
+    vals = rng.random(len(c)).astype(np.float32)
+    R = 16
+    A = []
+    for n, d in enumerate(dims):
+        a = rng.standard_normal((d, R)).astype(np.float32)
+        unused = np.setdiff1d(np.arange(d), c[:, n])
+        a[unused] = np.where(rng.random((len(unused), R)) < 0.5, np.inf, np.nan)
+        A.append(torch.from_numpy(a).cuda())
+    t = blco.Tensor.build(torch.from_numpy(c.astype(np.int32)).cuda(), torch.from_numpy(vals).cuda(), dims)
+    v64 = vals.astype(np.float64)
+    for n in range(3):
+        out = t.mttkrp(n, A).cpu().numpy()
+        used = np.unique(c[:, n])
+        Af = [a.cpu().numpy().astype(np.float64) for a in A]
+        M, S = oracle.mttkrp(c, v64, dims, Af, n)
+        assert np.isfinite(out).all()
+        assert oracle.max_rel_err(out[used], M[used], S[used]) <= FP32_TOL
+        assert np.all(out[np.setdiff1d(np.arange(dims[n]), used)] == 0.0)
+
+
 def test_convert_matches_oracle_rounding():
     x = torch.randn(100_003, device="cuda") * 3
     y = blco.convert(x, torch.bfloat16)
@@ -340,6 +369,25 @@ def test_gram_and_update_match_oracle():
     assert int(info.item()) == 0
     np.testing.assert_allclose(lam.cpu().numpy(), lref, rtol=1e-5)
     np.testing.assert_allclose(out.cpu().numpy(), ref / lref, rtol=1e-4, atol=1e-6)
+
+
+@pytest.mark.parametrize("R", [1, 5, 8, 33, 64, 128])
+def test_gram_float32_pairs_match_fp64(R):
+    """Grams of tall factors with a wide dynamic range (entries scaled by
+    10^-3..10^3 per row, signs mixed) against the FP64 oracle, normalised by
+    sum_i |A[i,r] A[i,c]|: the Dot2 accumulation must stay near 2^-48."""
+    rng = np.random.default_rng(R)
+    I = 200_003
+    A = (rng.standard_normal((I, R)) * 10.0 ** rng.uniform(-3, 3, (I, 1))).astype(np.float32)
+    G = torch.empty((R, R), dtype=torch.float64, device="cuda")
+    blco.blco_gram(torch.from_numpy(A).cuda(), blco.BLCO_F32, I, R, G)
+    A64 = A.astype(np.float64)
+    ref = oracle.gram(A64)
+    scale = np.abs(A64).T @ np.abs(A64)
+    err = np.max(np.abs(G.cpu().numpy() - ref) / scale)
+    assert err <= 1e-12, err
+    Gh = G.cpu().numpy()
+    assert np.max(np.abs(Gh - Gh.T) / scale) <= 1e-13  # symmetric up to the order of the CTA sums
 
 
 def test_update_pseudo_inverse_path():
