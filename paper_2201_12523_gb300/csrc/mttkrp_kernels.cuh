@@ -281,21 +281,27 @@ struct Stage {
 // -------------------------------------------------------------------------
 // MTTKRP
 // -------------------------------------------------------------------------
-// Resident CTAs per SM the register budget is sized for: 3 for the lighter
-// shapes (80 registers), 2 where wide ranks or many gathered modes need more.
+// Resident CTAs per SM the register budget is sized for (80 registers for
+// 3, 128 for 2). Measured on GB300: the MTTKRP kernel is fastest with 3 up
+// to R = 32 (also with 3 gathered modes: -10% at 4 modes) and with 2 at
+// R = 64; the CP-model kernel keeps 2 where it gathers 3 or more rows.
 template <int R, int NG>
-__host__ __device__ constexpr int min_ctas() {
+__host__ __device__ constexpr int mttkrp_min_ctas() {
+    return (R >= 64 || NG == 0) ? 2 : 3;
+}
+template <int R, int NG>
+__host__ __device__ constexpr int cp_min_ctas() {
     return (R >= 64 || NG == 0 || NG >= 3) ? 2 : 3;
 }
 
 template <typename T, int R, int NG, bool COMP>
-__global__ void __launch_bounds__(kThreads, min_ctas<R, NG>()) k_mttkrp(const KParams p) {
+__global__ void __launch_bounds__(kThreads, mttkrp_min_ctas<R, NG>()) k_mttkrp(const KParams p) {
     constexpr int VEC = lane_vec<T, R>();  // elements per lane
     constexpr int H = VEC / 2;   // packed pairs per lane
     constexpr int G = R / VEC;   // lanes per nonzero
     static_assert(G >= 1 && G <= 32 && (32 % G) == 0, "rank must give 1..32 lanes per row");
     constexpr int STEPS = G;     // sorted positions per subgroup (P = 32 / G subgroups)
-    constexpr int CH = STEPS < 32 / VEC ? STEPS : 32 / VEC;  // positions per register batch (32 floats)
+    constexpr int CH = STEPS < 16 / VEC ? STEPS : 16 / VEC;  // positions per register batch (16 floats)
     constexpr int NS = gather_slots<NG>();
 
     extern __shared__ __align__(16) unsigned char smem[];
@@ -551,7 +557,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<R, NG>()) k_mttkrp(const KP
 // CP model at the nonzeros: xhat = sum_r prod_n A_n[i_n, r] (all N modes gathered)
 // -------------------------------------------------------------------------
 template <typename T, int R, int NG>
-__global__ void __launch_bounds__(kThreads, min_ctas<R, NG>()) k_cp_fwd(const KParams p) {
+__global__ void __launch_bounds__(kThreads, cp_min_ctas<R, NG>()) k_cp_fwd(const KParams p) {
     constexpr int VEC = lane_vec<T, R>();
     constexpr int H = VEC / 2;
     constexpr int G = R / VEC;
