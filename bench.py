@@ -275,6 +275,7 @@ def time_steps(step, K: int, stream) -> float:
     return e0.elapsed_time(e1)
 
 
+CPU_SAMPLE_NNZ = 10_000_000  # oracle baseline sample: about 10 s of one core per all-mode pass
 STREAMED = {"zipf1.2-5d-1B": 16 << 30}  # workloads run out of core: device budget in bytes
 CP_MODEL = "cp-planted-3d-200M"
 
@@ -344,8 +345,8 @@ def run_blco(args, ranks: Ranks):
     t_plain = None
     if not args.no_bf16 and not info["streamed"]:
         t_plain = blco.Tensor.build(coords, vals, spec.dims, plain_sums=True)
-    coords_h = coords[: min(spec.nnz, 1_000_000)].cpu()
-    vals_h = vals[: min(spec.nnz, 1_000_000)].cpu()
+    coords_h = coords[: min(spec.nnz, CPU_SAMPLE_NNZ)].cpu()
+    vals_h = vals[: min(spec.nnz, CPU_SAMPLE_NNZ)].cpu()
     del coords, vals
     torch.cuda.empty_cache()
 
@@ -499,7 +500,7 @@ def run_blco(args, ranks: Ranks):
 
     cpu = None
     if not args.no_cpu and ranks.rank == 0:
-        sample = min(spec.nnz, 1_000_000)
+        sample = min(spec.nnz, CPU_SAMPLE_NNZ)
         rate, sec = cpu_oracle_rate(spec, coords_h, vals_h, A, sample)
         cpu = {"value": rate, "unit": "nnz/s (all-mode)", "cores": 1, "kind": "oracle",
                "sample": f"first {sample} nonzeros of the workload (random order), all {spec.order} modes, "

@@ -93,7 +93,9 @@ typedef struct {
     int64_t max_nnz_per_block;
     int64_t queue_nnz;                     /* per-queue reservation (streamed stores) */
     int32_t n_queues;
-    int32_t hot_rows[BLCO_MAX_MODES];      /* rows per mode accumulated on chip */
+    int32_t hot_rows[BLCO_MAX_MODES];      /* hottest rows kept per mode (a launch at rank R
+                                              accumulates the first min(this, 1024 / R)
+                                              of them on chip) */
     int64_t device_bytes;                  /* device memory held by the handle */
     int64_t host_bytes;                    /* pinned host memory held by the handle */
 } blco_info_t;
