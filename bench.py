@@ -47,8 +47,8 @@ FALLBACK_HBM_GBS = 6800.0
 
 # DRAM traffic of the MTTKRP kernel from an ncu capture (profiles/), valid only
 # for the kernel source it was taken from (sha256 of csrc/mttkrp.cu).
-TRAFFIC_RECORD = {"mttkrp_src_sha256": "89751c630be816f0edb7c4e49a8600124376fc5ad881e58099de32d8d274b06d",
-                  "bytes_per_launch": 4.603e9}  # mean of modes 0/1/2 at 150M nonzeros, R = 32, FP32
+TRAFFIC_RECORD = {"mttkrp_src_sha256": "feaf50f7600912613d17babf1c5c9d382454222256a202e661f8dd295ca657b6",
+                  "bytes_per_launch": 4.485e9}  # mean of modes 0/1/2 at 150M nonzeros, R = 32, FP32
 
 
 def parse_args(argv=None):
