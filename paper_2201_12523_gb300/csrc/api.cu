@@ -110,7 +110,9 @@ struct blco_tensor {
     uint64_t *q_keys[8] = {};
     float *q_vals[8] = {};
     cudaStream_t q_stream[8] = {};
-    cudaEvent_t q_done[8] = {};
+    cudaEvent_t q_done[8] = {};    // after each kernel on the queue: its reservation is free
+    cudaEvent_t q_copied[8] = {};  // after each batch upload into the queue's reservation
+    cudaStream_t q_up = nullptr;   // all batch uploads, one after another
     cudaEvent_t ev_fork = nullptr;
     struct Batch {
         int64_t begin, end;
@@ -200,8 +202,10 @@ void release(blco_tensor *h) {
         h->dfree(h->q_vals[q], 0);
         if (h->q_stream[q]) cudaStreamDestroy(h->q_stream[q]);
         if (h->q_done[q]) cudaEventDestroy(h->q_done[q]);
+        if (h->q_copied[q]) cudaEventDestroy(h->q_copied[q]);
     }
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->q_up) cudaStreamDestroy(h->q_up);
     if (h->up) cudaStreamDestroy(h->up);
     if (h->down) cudaStreamDestroy(h->down);
     for (cudaEvent_t ev : {h->ev_call, h->ev_down})
@@ -322,15 +326,19 @@ blco_status over_store(blco_tensor *h, const char *name, const float *vals_ext, 
         if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
         return BLCO_OK;
     }
-    // The copies into a queue's reservation only wait for that queue's
-    // previous kernel (stream order), so they may start while earlier work on
-    // `s` (the previous mode, the output zeroing) is still running; each
-    // queue's first kernel of this call waits for `s`. Whatever happens, every
-    // queue that received work is joined back into `s` before returning, so
-    // no work of a failed call outlives it on the queues.
+    // Batches go through the queues round-robin. All uploads run on one
+    // stream (q_up), back to back: concurrent host-to-device copies on
+    // several streams share the link less efficiently than one stream. An
+    // upload into a queue's reservation waits only for the previous kernel
+    // on that queue (q_done), so uploads run ahead across modes; the kernel
+    // waits for its upload (q_copied) and, the first time in this call, for
+    // earlier work on `s` (ev_fork: the output zeroing, the previous mode).
+    // Whatever happens, the queues and the upload stream that received work
+    // are joined back into `s` before returning, so no work of a failed
+    // call outlives it.
     cudaError_t e = cudaEventRecord(h->ev_fork, s);
     if (e != cudaSuccess) return cuda_fail(e, "event record");
-    bool used[8] = {};
+    bool used[8] = {}, uploaded = false;
     blco_status st = BLCO_OK;
     for (size_t b = 0; b < h->batches.size() && st == BLCO_OK; ++b) {
         const int q = (int)(b % h->nq);
@@ -340,16 +348,21 @@ blco_status over_store(blco_tensor *h, const char *name, const float *vals_ext, 
             st = fail(BLCO_ERR_CUDA, "injected host-to-device copy fault");
             break;
         }
-        e = cudaMemcpyAsync(h->q_keys[q], h->h_keys + bt.begin, sizeof(uint64_t) * n, cudaMemcpyHostToDevice,
-                            h->q_stream[q]);
+        e = cudaStreamWaitEvent(h->q_up, h->q_done[q], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h->q_keys[q], h->h_keys + bt.begin, sizeof(uint64_t) * n, cudaMemcpyHostToDevice,
+                                h->q_up);
         if (e == cudaSuccess && !vals_ext)
             e = cudaMemcpyAsync(h->q_vals[q], h->h_vals + bt.begin, sizeof(float) * n, cudaMemcpyHostToDevice,
-                                h->q_stream[q]);
-        used[q] = true;
+                                h->q_up);
+        if (e == cudaSuccess) e = cudaEventRecord(h->q_copied[q], h->q_up);
+        uploaded = true;
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->q_stream[q], h->q_copied[q], 0);
         if (e != cudaSuccess) {
             st = cuda_fail(e, "queue upload");
             break;
         }
+        used[q] = true;
         StoreView sv = h->view();
         sv.keys = h->q_keys[q];
         sv.key_origin = bt.begin;
@@ -370,6 +383,7 @@ blco_status over_store(blco_tensor *h, const char *name, const float *vals_ext, 
             }
         }
         e = launch(sv, h->q_stream[q]);
+        if (e == cudaSuccess) e = cudaEventRecord(h->q_done[q], h->q_stream[q]);
         if (e != cudaSuccess) st = cuda_fail(e, "kernel launch");
     }
     for (int q = 0; q < h->nq; ++q) {
@@ -377,6 +391,11 @@ blco_status over_store(blco_tensor *h, const char *name, const float *vals_ext, 
         e = cudaEventRecord(h->q_done[q], h->q_stream[q]);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->q_done[q], 0);
         if (e != cudaSuccess && st == BLCO_OK) st = cuda_fail(e, "queue join");
+    }
+    if (uploaded) {  // an upload whose kernel was never launched (an error) must not outlive the call
+        e = cudaEventRecord(h->ev_fork, h->q_up);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_fork, 0);
+        if (e != cudaSuccess && st == BLCO_OK) st = cuda_fail(e, "upload join");
     }
     return st;
 }
@@ -594,8 +613,10 @@ blco_status blco_build(const uint32_t *coords, const float *vals, int64_t nnz, c
                 if (e == cudaSuccess) e = h->dalloc((void **)&h->q_vals[q], sizeof(float) * h->queue_nnz);
                 if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->q_stream[q], cudaStreamNonBlocking);
                 if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->q_done[q], cudaEventDisableTiming);
+                if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->q_copied[q], cudaEventDisableTiming);
             }
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->q_up, cudaStreamNonBlocking);
             if (e != cudaSuccess) BAIL(cuda_fail(e, "queue reservation"));
             // batches: consecutive whole blocks up to the reservation (Section 4.2)
             int64_t b0 = 0;
