@@ -403,6 +403,7 @@ def run_blco(args, ranks: Ranks):
     launches, kms = prof.get("mttkrp", (0, 0.0))
     zl, zms = prof.get("zero", (0, 0.0))
     fl, fms = prof.get("cp_fwd", (0, 0.0))
+    sl, sms = prof.get("sum_copies", (0, 0.0))
     bytes_all = sum(algorithmic_bytes(spec, R, 4, n) for n in range(spec.order))
     per_launch_bytes = bytes_all / spec.order
     per_launch_ms = kms / max(launches, 1)
@@ -519,7 +520,7 @@ def run_blco(args, ranks: Ranks):
                        "parallelism": f"replicas x{ranks.world}",
                        "l2": "inputs larger than L2, no flush"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": int(launches + zl + fl),
+            "gpu_launches": int(launches + zl + fl + sl),
             "build_ms": build_ms, "gen_s": gen_s,
             "construction": {"ms": build_ms, "nnz_per_s": spec.nnz / (build_ms / 1e3),
                              "all_mode_steps_to_amortize": build_ms / ms_per_step,

@@ -121,6 +121,9 @@ struct blco_tensor {
     // staging workspace for host arguments
     void *ws = nullptr;
     size_t ws_bytes = 0;
+    // private output copies of short modes (grown on demand)
+    float *d_copies = nullptr;
+    size_t copies_bytes = 0;
     // host-argument copies of blco_mttkrp_all (created on first use): uploads
     // and downloads on their own streams, so they overlap other modes' kernels
     cudaStream_t up = nullptr, down = nullptr;
@@ -219,6 +222,7 @@ void release(blco_tensor *h) {
         cudaEventDestroy(m.b);
     }
     h->dfree(h->ws, 0);
+    h->dfree(h->d_copies, 0);
     if (h->h_keys) cudaFreeHost(h->h_keys);
     if (h->h_vals) cudaFreeHost(h->h_vals);
     if (h->h_perm) cudaFreeHost(h->h_perm);
@@ -415,14 +419,47 @@ HotRows hot_for(const blco_tensor *h, int mode, int R) {
     return hr;
 }
 
+// Device memory for n private output copies of `floats` each; false (and
+// no error left pending) when it cannot be had, e.g. under a device budget.
+bool copy_buffer(blco_tensor *h, size_t bytes, float **p) {
+    if (bytes > h->copies_bytes) {
+        h->dfree(h->d_copies, h->copies_bytes);
+        h->d_copies = nullptr;
+        h->copies_bytes = 0;
+        if (h->dalloc((void **)&h->d_copies, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            h->d_copies = nullptr;
+            return false;
+        }
+        h->copies_bytes = bytes;
+    }
+    *p = h->d_copies;
+    return true;
+}
+
 blco_status mttkrp_device(blco_tensor *h, int mode, const FactorSet &fs, blco_dtype fdt, int R, float *out,
                           const float *vals_ext, cudaStream_t s) {
-    cudaError_t e = timed(h, "zero", s, [&]() { return launch_zero(out, h->L.dims[mode] * (int64_t)R, s); });
-    if (e != cudaSuccess) return cuda_fail(e, "zero output");
+    const int64_t n = h->L.dims[mode] * (int64_t)R;
     const HotRows hot = hot_for(h, mode, R);
-    return over_store(h, "mttkrp", vals_ext, s, [&](const StoreView &sv, cudaStream_t st) {
-        return launch_mttkrp(sv, fs, fdt, R, mode, hot, out, h->compensated, st);
+    // short modes: reduce into one private copy per SM, then sum the copies
+    OutCopies oc;
+    float *dst = out;
+    const int nc = hot.dense ? 1 : output_copies(h->L.dims[mode], R);
+    if (nc > 1 && copy_buffer(h, sizeof(float) * (size_t)nc * n, &dst)) {
+        oc.n = nc;
+        oc.stride = n;
+    } else {
+        dst = out;
+    }
+    cudaError_t e = timed(h, "zero", s, [&]() { return launch_zero(dst, n * oc.n, s); });
+    if (e != cudaSuccess) return cuda_fail(e, "zero output");
+    blco_status st = over_store(h, "mttkrp", vals_ext, s, [&](const StoreView &sv, cudaStream_t q) {
+        return launch_mttkrp(sv, fs, fdt, R, mode, hot, dst, oc, h->compensated, q);
     });
+    if (st != BLCO_OK || oc.n == 1) return st;
+    e = timed(h, "sum_copies", s, [&]() { return launch_sum_copies(dst, oc.n, n, out, s); });
+    if (e != cudaSuccess) return cuda_fail(e, "sum of output copies");
+    return BLCO_OK;
 }
 
 blco_status check_common(blco_tensor *h, blco_dtype fdt, int R) {

@@ -426,7 +426,31 @@ __global__ void __launch_bounds__(256) k_norm2(const float *__restrict__ v, int6
     if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
 }
 
+// out = sum of the private output copies (n floats each, n % 4 == 0,
+// 16-byte aligned), one float4 per thread and step; copies summed in order.
+__global__ void k_sum_copies(const float4 *__restrict__ copies, int ncopies, int64_t n4, float4 *__restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+        float4 a = copies[i];
+        for (int c = 1; c < ncopies; ++c) {
+            const float4 b = copies[(int64_t)c * n4 + i];
+            a.x += b.x;
+            a.y += b.y;
+            a.z += b.z;
+            a.w += b.w;
+        }
+        out[i] = a;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_sum_copies(const float *copies, int ncopies, int64_t n, float *out, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int64_t n4 = n / 4;
+    k_sum_copies<<<grid_cap(n4, 256), 256, 0, s>>>(reinterpret_cast<const float4 *>(copies), ncopies, n4,
+                                                    reinterpret_cast<float4 *>(out));
+    return cudaGetLastError();
+}
 
 cudaError_t launch_zero(float *p, int64_t n, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;

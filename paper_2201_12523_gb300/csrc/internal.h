@@ -62,20 +62,29 @@ struct HotRows {
     int dense;             // 1 = every row of the mode is accumulated on chip (slot == row)
 };
 
+// Private copies of a short mode's output: CTA b of a launch reduces into
+// copy b % n (n == 1: into the output itself); the copies are summed into the
+// output afterwards (launch_sum_copies).
+struct OutCopies {
+    int n = 1;
+    int64_t stride = 0;  // floats between copies (I_mode * R)
+};
+
 // ----------------------------------------------------------------- kernels
 // mttkrp.cu (dispatch by factor type). With 16-bit factors `compensated`
 // selects Kahan-compensated run sums; float32 factors always sum plainly.
 cudaError_t launch_mttkrp(const StoreView &sv, const FactorSet &fs, blco_dtype fdt, int R, int mode,
-                          const HotRows &hot, float *out, bool compensated, cudaStream_t s);
+                          const HotRows &hot, float *out, const OutCopies &oc, bool compensated, cudaStream_t s);
+int output_copies(int64_t I, int R);  // private output copies worth keeping for a mode (1 = none)
 cudaError_t launch_cp_fwd(const StoreView &sv, const FactorSet &fs, blco_dtype fdt, int R,
                           float *xhat, int64_t xhat_origin, cudaStream_t s);
 // mttkrp_f32.cu, mttkrp_bf16.cu, mttkrp_f16.cu (one factor type each)
 cudaError_t launch_mttkrp_f32(const StoreView &sv, const FactorSet &fs, int R, int mode, const HotRows &hot,
-                              float *out, cudaStream_t s);
+                              float *out, const OutCopies &oc, cudaStream_t s);
 cudaError_t launch_mttkrp_bf16(const StoreView &sv, const FactorSet &fs, int R, int mode, const HotRows &hot,
-                               float *out, bool compensated, cudaStream_t s);
+                               float *out, const OutCopies &oc, bool compensated, cudaStream_t s);
 cudaError_t launch_mttkrp_f16(const StoreView &sv, const FactorSet &fs, int R, int mode, const HotRows &hot,
-                              float *out, bool compensated, cudaStream_t s);
+                              float *out, const OutCopies &oc, bool compensated, cudaStream_t s);
 cudaError_t launch_cp_fwd_f32(const StoreView &sv, const FactorSet &fs, int R, float *xhat, int64_t xorigin,
                               cudaStream_t s);
 cudaError_t launch_cp_fwd_bf16(const StoreView &sv, const FactorSet &fs, int R, float *xhat, int64_t xorigin,
@@ -107,6 +116,7 @@ cudaError_t top_rows(const uint32_t *counts, int64_t I, int k, uint32_t *rows_ou
 
 // dense.cu
 cudaError_t launch_zero(float *p, int64_t n, cudaStream_t s);
+cudaError_t launch_sum_copies(const float *copies, int ncopies, int64_t n, float *out, cudaStream_t s);
 cudaError_t launch_convert(const float *src, void *dst, blco_dtype dt, int64_t n, cudaStream_t s);
 cudaError_t launch_gram(const void *A, blco_dtype fdt, int64_t I, int R, double *G, cudaStream_t s);
 cudaError_t launch_cpals_update(const double *const *grams, int N, int mode, int R, const float *M,

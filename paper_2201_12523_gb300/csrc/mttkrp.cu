@@ -10,13 +10,27 @@ bool rank_supported(int R) { return R == 8 || R == 16 || R == 32 || R == 64 || R
 int warp_tier_capacity(int R) { return rank_supported(R) ? warp_tier_rows(R) : 0; }
 
 cudaError_t launch_mttkrp(const StoreView &sv, const FactorSet &fs, blco_dtype fdt, int R, int mode,
-                          const HotRows &hot, float *out, bool compensated, cudaStream_t s) {
+                          const HotRows &hot, float *out, const OutCopies &oc, bool compensated, cudaStream_t s) {
     switch (fdt) {
-        case BLCO_F32: return launch_mttkrp_f32(sv, fs, R, mode, hot, out, s);
-        case BLCO_BF16: return launch_mttkrp_bf16(sv, fs, R, mode, hot, out, compensated, s);
-        case BLCO_F16: return launch_mttkrp_f16(sv, fs, R, mode, hot, out, compensated, s);
+        case BLCO_F32: return launch_mttkrp_f32(sv, fs, R, mode, hot, out, oc, s);
+        case BLCO_BF16: return launch_mttkrp_bf16(sv, fs, R, mode, hot, out, oc, compensated, s);
+        case BLCO_F16: return launch_mttkrp_f16(sv, fs, R, mode, hot, out, oc, compensated, s);
     }
     return cudaErrorInvalidValue;
+}
+
+// A short mode's output receives most of a launch's reductions on few rows;
+// one private copy per SM spreads them. Measured on GB300: at R = 64 (16
+// rows per warp on chip, 16 vector reductions per nonzero) a 1024-row mode
+// ran 18% faster with copies; at R = 32 (32 rows on chip) 256- and
+// 2048-row modes did not gain. Copies are used from R = 64, while all of
+// them together stay well inside L2 (48 MB) and the mode is not held on chip
+// entirely (the per-warp copies cover modes of at most 1024 / R rows).
+int output_copies(int64_t I, int R) {
+    const int64_t bytes = I * (int64_t)R * (int64_t)sizeof(float);
+    const int n = sm_count();
+    if (R < 64 || I <= warp_tier_capacity(R) || bytes * n > ((int64_t)48 << 20)) return 1;
+    return n;
 }
 
 cudaError_t launch_cp_fwd(const StoreView &sv, const FactorSet &fs, blco_dtype fdt, int R, float *xhat,

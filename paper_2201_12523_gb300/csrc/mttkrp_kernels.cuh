@@ -75,6 +75,10 @@ struct KParams {
     int t_mode;
     float *out;
     int64_t out_origin;
+    // MTTKRP into private output copies (short modes): CTA b adds into copy
+    // b % ncopies, copy_stride floats apart; ncopies == 1 means `out` itself
+    int ncopies;
+    int64_t copy_stride;
     // on-chip accumulation of the hottest rows: the first kw rows of
     // hot_rows get one private copy per warp; with hot_dense every row of
     // the mode does and slot == row
@@ -321,6 +325,7 @@ __global__ void __launch_bounds__(kThreads, mttkrp_min_ctas<R, NG>()) k_mttkrp(c
     Stage<NG> &st = stage[wid];
     float *wacc = wacc_all + (size_t)wid * kw * R;
     const int ng = n_gather<NG>(p);
+    float *const outp = p.out + (p.ncopies > 1 ? (size_t)(blockIdx.x % p.ncopies) * p.copy_stride : 0);
 
     // --- zero the accumulators, build the hot-row table: one hash, buckets
     // of 8 row ids filled in order of decreasing count by warp 0; a row that
@@ -499,7 +504,7 @@ __global__ void __launch_bounds__(kThreads, mttkrp_min_ctas<R, NG>()) k_mttkrp(c
                         float sv[VEC];
 #pragma unroll
                         for (int h = 0; h < H; ++h) unpack2(sum[h], sv[2 * h], sv[2 * h + 1]);
-                        float *o2 = p.out + (size_t)row * R + c * VEC;
+                        float *o2 = outp + (size_t)row * R + c * VEC;
 #pragma unroll
                         for (int e = 0; e < VEC; e += 4)
                             red_add_v4(o2 + e, sv[e], sv[e + 1], sv[e + 2], sv[e + 3]);
@@ -549,7 +554,7 @@ __global__ void __launch_bounds__(kThreads, mttkrp_min_ctas<R, NG>()) k_mttkrp(c
         }
         const uint32_t row = p.hot_dense ? (uint32_t)sl : __ldg(p.hot_rows + sl);
         if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f)
-            red_add_v4(p.out + (size_t)row * R + q * 4, v.x, v.y, v.z, v.w);
+            red_add_v4(outp + (size_t)row * R + q * 4, v.x, v.y, v.z, v.w);
     }
 }
 
@@ -738,7 +743,7 @@ cudaError_t by_rank_cp(const KParams &p, int R, cudaStream_t s) {
 
 template <typename T>
 cudaError_t mttkrp_as(const StoreView &sv, const FactorSet &fs, int R, int mode, const HotRows &hot, float *out,
-                      bool compensated, cudaStream_t s) {
+                      const OutCopies &oc, bool compensated, cudaStream_t s) {
     if (sv.end <= sv.begin) return cudaSuccess;
     KParams p = make_params(sv);
     p.t_shift = sv.shift[mode];
@@ -755,6 +760,8 @@ cudaError_t mttkrp_as(const StoreView &sv, const FactorSet &fs, int R, int mode,
     }
     p.n_gather = q;
     p.out = out;
+    p.ncopies = oc.n > 1 ? oc.n : 1;
+    p.copy_stride = oc.stride;
     if (hot.dense) {
         // every row of the mode fits the warp tier: slot == row, no table
         p.hot_dense = 1;

@@ -232,6 +232,19 @@ def test_streamed_store_matches(nq):
     _store_equal(t, coords, vals, spec.dims, 64, 4000)
 
 
+@pytest.mark.parametrize("streamed", [False, True])
+def test_short_mode_output_copies(streamed):
+    """R = 64 with 1024- and 600-row modes: those launches reduce into one
+    private output copy per SM and sum the copies afterwards, also when the
+    batches of a streamed store run concurrently on several queues."""
+    spec = synth.small(4, 150_000, (1 << 16, 600, 1 << 10))
+    coords, vals, A = make(spec)
+    kw = dict(force_stream=True, max_nnz_per_block=4000, n_queues=4) if streamed else {}
+    t = blco.Tensor.build(coords, vals, spec.dims, **kw)
+    check_mttkrp_all(t, coords, vals, A, spec.dims)
+    check_mttkrp_all(t, coords, vals, A, spec.dims, modes=[2, 1])  # again: copies reused
+
+
 def test_budget_forces_streaming():
     spec = synth.small(1, 200_000, (1 << 16, 1 << 15, 1 << 11))
     coords, vals, A = make(spec)
