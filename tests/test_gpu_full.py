@@ -114,6 +114,7 @@ def test_zipf4d_500M_fp32_and_bf16():
     torch.cuda.empty_cache()
     _tick("generated")
     t = blco.Tensor.build(coords, vals, spec.dims)
+    tp = blco.Tensor.build(coords, vals, spec.dims, plain_sums=True)
     c, v = _host(coords, vals)
     del coords, vals
     _tick("built")
@@ -126,8 +127,10 @@ def test_zipf4d_500M_fp32_and_bf16():
     A16 = [blco.convert(a, torch.bfloat16) for a in A]
     e16 = _sampled_mttkrp(t, spec.dims, A16, rows, ref32, BF16_TOL, "zipf4d bf16 vs unrounded")
     e16r = _sampled_mttkrp(t, spec.dims, A16, rows, ref16, FP32_TOL, "zipf4d bf16 vs rounded")
+    e16p = _sampled_mttkrp(tp, spec.dims, A16, rows, ref16, FP32_TOL, "zipf4d bf16 plain sums vs rounded")
     print("per-mode max rel err f32:", [f"{e:.2e}" for e in e32], "bf16:", [f"{e:.2e}" for e in e16],
-          "bf16 (rounded factors):", [f"{e:.2e}" for e in e16r])
+          "bf16 (rounded factors), compensated runs:", [f"{e:.2e}" for e in e16r],
+          "plain runs:", [f"{e:.2e}" for e in e16p])
     _tick("done")
 
 

@@ -125,6 +125,26 @@ def test_mttkrp_skewed_f32(idx, nnz, dims):
     check_mttkrp_all(t, coords, vals, A, spec.dims)
 
 
+@pytest.mark.parametrize("dims,R", [
+    ((1 << 16, 1 << 15, 1 << 14, 1 << 13, 1 << 12, 1 << 11), 16),   # 6 modes, 81 index bits
+    ((1 << 16,) * 8, 8),                                            # 8 modes, 128 index bits
+    ((1 << 16,) * 8, 32),
+])
+def test_many_modes_generic_path(dims, R):
+    """6 and 8 modes take the kernel's run-time gather count (5 or 7
+    gathered rows); 128 index bits fill both key words before blocking."""
+    rng = np.random.default_rng(len(dims) * 100 + R)
+    nnz = 30_011
+    c = np.stack([rng.integers(0, d, nnz) for d in dims], 1).astype(np.int32)
+    vals = rng.random(nnz).astype(np.float32)
+    A = [torch.from_numpy(rng.standard_normal((d, R)).astype(np.float32)).cuda() for d in dims]
+    coords = torch.from_numpy(c).cuda()
+    t = blco.Tensor.build(coords, torch.from_numpy(vals).cuda(), dims, max_nnz_per_block=7000)
+    assert t.info()["total_bits"] == sum(int(np.ceil(np.log2(d))) for d in dims)
+    _store_equal(t, coords, torch.from_numpy(vals), dims, 64, 7000)
+    check_mttkrp_all(t, coords, torch.from_numpy(vals), A, dims)
+
+
 def test_mttkrp_positive_heavy_rows():
     """All terms positive on a Zipf head (the hardest case for float32 sums)."""
     spec = synth.small(1, 400_000, (1 << 12, 1 << 11, 1 << 11))
