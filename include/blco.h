@@ -35,8 +35,10 @@
  *     enqueued GPU work surface as BLCO_ERR_CUDA on a later call or on
  *     blco_sync. blco_last_error() gives a message for the calling thread.
  *   - The caller owns every pointer it passes; the handle owns the store,
- *     its block table, queue buffers and workspace, all freed by
- *     blco_destroy. A handle may be used by one thread at a time.
+ *     its block table, queue buffers, output copies and workspace, all freed
+ *     by blco_destroy. A handle may be used by one thread at a time, and its
+ *     calls must not overlap on the GPU: calls on different streams share
+ *     those buffers, so order them (one stream, or events).
  */
 #ifndef BLCO_H
 #define BLCO_H
