@@ -20,17 +20,18 @@ cudaError_t launch_mttkrp(const StoreView &sv, const FactorSet &fs, blco_dtype f
 }
 
 // A short mode's output receives most of a launch's reductions on few rows;
-// one private copy per SM spreads them. Measured on GB300: at R = 64 (16
-// rows per warp on chip, 16 vector reductions per nonzero) a 1024-row mode
-// ran 18% faster with copies; at R = 32 (32 rows on chip) 256- and
-// 2048-row modes did not gain. Copies are used from R = 64, while all of
-// them together stay well inside L2 (48 MB) and the mode is not held on chip
-// entirely (the per-warp copies cover modes of at most 1024 / R rows).
+// private copies spread them. Measured on GB300: at R = 64 (16 rows per warp
+// on chip, 16 vector reductions per nonzero) a 1024-row mode ran 18% faster
+// with one copy per SM and 21% faster with 16 copies (less L2 taken from the
+// factor-row gathers); at R = 32 (32 rows on chip) 256- and 2048-row modes
+// gained nothing with 16, 32 or 152 copies. So: 16 copies from R = 64, while
+// they fit in 48 MB and the mode is not held on chip entirely (the per-warp
+// copies cover modes of at most 1024 / R rows).
 int output_copies(int64_t I, int R) {
+    constexpr int kCopies = 16;
     const int64_t bytes = I * (int64_t)R * (int64_t)sizeof(float);
-    const int n = sm_count();
-    if (R < 64 || I <= warp_tier_capacity(R) || bytes * n > ((int64_t)48 << 20)) return 1;
-    return n;
+    if (R < 64 || I <= warp_tier_capacity(R) || bytes * kCopies > ((int64_t)48 << 20)) return 1;
+    return kCopies;
 }
 
 cudaError_t launch_cp_fwd(const StoreView &sv, const FactorSet &fs, blco_dtype fdt, int R, float *xhat,

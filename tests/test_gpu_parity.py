@@ -254,8 +254,8 @@ def test_streamed_store_matches(nq):
 
 @pytest.mark.parametrize("streamed", [False, True])
 def test_short_mode_output_copies(streamed):
-    """R = 64 with 1024- and 600-row modes: those launches reduce into one
-    private output copy per SM and sum the copies afterwards, also when the
+    """R = 64 with 1024- and 600-row modes: those launches reduce into
+    private output copies and sum the copies afterwards, also when the
     batches of a streamed store run concurrently on several queues."""
     spec = synth.small(4, 150_000, (1 << 16, 600, 1 << 10))
     coords, vals, A = make(spec)
