@@ -51,3 +51,22 @@ def test_two_gloo_ranks_aggregate_as_replicas():
         assert out[r]["rate"] == pytest.approx(300.0 / 4.0)
     # the oracle arm runs on rank 0 only; the other ranks return at once
     assert out[1]["reference_rc"] == 0
+
+
+def test_reference_arm_line_on_cpu(capsys):
+    """The reference arm (the oracle) prints the benchmark's JSON line with
+    the keys the contract asks for; run here on the small uniform workload."""
+    import json
+
+    import bench
+
+    rc = bench.main(["--impl", "reference", "--workload", "uniform-3d-100k", "--steps", "1", "--warmup", "0"])
+    assert rc == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["config"]["workload"] == "uniform-3d-100k"
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
