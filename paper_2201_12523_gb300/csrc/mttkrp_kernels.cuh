@@ -274,12 +274,21 @@ __host__ __device__ __forceinline__ SmemLayout smem_layout(size_t stage_bytes, i
     return L;
 }
 
+// The MTTKRP kernel's staging of one tile's sorted positions: gathered row
+// ids and values by field, the target row and its on-chip slot as one 8-byte
+// word (read with one shared load where a run ends).
+template <int NG>
+struct MStage {
+    uint32_t idx[gather_slots<NG>()][32];
+    float val[32];
+    uint2 rs[32];  // (row, slot)
+};
+
+// The CP-model kernel's staging: gathered row ids in, model values out.
 template <int NG>
 struct Stage {
     uint32_t idx[gather_slots<NG>()][32];
     float val[32];
-    uint32_t row[32];
-    int32_t slot[32];
 };
 
 // -------------------------------------------------------------------------
@@ -311,8 +320,8 @@ __global__ void __launch_bounds__(kThreads, mttkrp_min_ctas<R, NG>()) k_mttkrp(c
     extern __shared__ __align__(16) unsigned char smem[];
     const int kw = p.kw;  // warp tier: the hottest rows, one private copy per warp
     const int nb = p.log2nb >= 0 ? (1 << p.log2nb) : 0;  // buckets of 8 row ids
-    const SmemLayout L = smem_layout(sizeof(Stage<NG>), kw, R, nb);
-    Stage<NG> *stage = reinterpret_cast<Stage<NG> *>(smem);
+    const SmemLayout L = smem_layout(sizeof(MStage<NG>), kw, R, nb);
+    MStage<NG> *stage = reinterpret_cast<MStage<NG> *>(smem);
     float *wacc_all = reinterpret_cast<float *>(smem + L.wacc);
     uint32_t *bkey = reinterpret_cast<uint32_t *>(smem + L.bkey);
     uint16_t *bslot = reinterpret_cast<uint16_t *>(smem + L.bslot);
@@ -322,7 +331,7 @@ __global__ void __launch_bounds__(kThreads, mttkrp_min_ctas<R, NG>()) k_mttkrp(c
     const int wid = threadIdx.x >> 5;
     const int g = lane / G;
     const int c = lane % G;
-    Stage<NG> &st = stage[wid];
+    MStage<NG> &st = stage[wid];
     float *wacc = wacc_all + (size_t)wid * kw * R;
     const int ng = n_gather<NG>(p);
     float *const outp = p.out + (p.ncopies > 1 ? (size_t)(blockIdx.x % p.ncopies) * p.copy_stride : 0);
@@ -442,8 +451,7 @@ __global__ void __launch_bounds__(kThreads, mttkrp_min_ctas<R, NG>()) k_mttkrp(c
         for (int q = 0; q < NS; ++q)
             if (q < ng) st.idx[q][spos] = o[q];
         st.val[spos] = val;
-        st.row[spos] = t;
-        st.slot[spos] = slot;
+        st.rs[spos] = make_uint2(t, (uint32_t)slot);
         __syncwarp();
 
         // --- rank-parallel products; subgroup g walks the sorted positions
@@ -495,8 +503,9 @@ __global__ void __launch_bounds__(kThreads, mttkrp_min_ctas<R, NG>()) k_mttkrp(c
                     f2 sum[H];
 #pragma unroll
                     for (int h = 0; h < H; ++h) sum[h] = acc[h].value();
-                    const uint32_t row = st.row[s];
-                    const int sl = st.slot[s];
+                    const uint2 rsw = st.rs[s];
+                    const uint32_t row = rsw.x;
+                    const int sl = (int)rsw.y;
                     const bool warp_tier = sl >= 0;
                     // continuation parts at the last step: atomics first
                     const bool cont = last && !run_end && warp_tier;
@@ -680,7 +689,7 @@ int grid_for(const void *kern, size_t shm, int64_t span) {
 template <typename T, int R, int NG, bool COMP>
 cudaError_t run_mttkrp_impl(const KParams &p, cudaStream_t s) {
     const int nb = p.log2nb >= 0 ? (1 << p.log2nb) : 0;
-    const size_t shm = smem_layout(sizeof(Stage<NG>), p.kw, R, nb).total;
+    const size_t shm = smem_layout(sizeof(MStage<NG>), p.kw, R, nb).total;
     auto kern = k_mttkrp<T, R, NG, COMP>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
     if (e != cudaSuccess) return e;
