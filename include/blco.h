@@ -275,7 +275,8 @@ blco_status blco_norm2(blco_handle h, double *out, blco_stream stream);
  * enabled, the handle records a CUDA event pair on the launching stream
  * around each kernel it launches. blco_profile_read waits for the recorded
  * events and returns one entry per kernel kind ("zero", "mttkrp", "sum_copies", "cp_fwd",
- * "norm2") with the number of launches and their summed duration, then
+ * "norm2"; "upload" for the batch copies of a streamed store) with the
+ * number of launches and their summed duration, then
  * clears the record. count receives the number of entries written (at most
  * capacity). Enabling costs two event records per launch.
  */

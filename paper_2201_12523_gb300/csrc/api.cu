@@ -354,11 +354,14 @@ blco_status over_store(blco_tensor *h, const char *name, const float *vals_ext, 
         }
         e = cudaStreamWaitEvent(h->q_up, h->q_done[q], 0);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(h->q_keys[q], h->h_keys + bt.begin, sizeof(uint64_t) * n, cudaMemcpyHostToDevice,
-                                h->q_up);
-        if (e == cudaSuccess && !vals_ext)
-            e = cudaMemcpyAsync(h->q_vals[q], h->h_vals + bt.begin, sizeof(float) * n, cudaMemcpyHostToDevice,
-                                h->q_up);
+            e = timed(h, "upload", h->q_up, [&]() {
+                cudaError_t ce = cudaMemcpyAsync(h->q_keys[q], h->h_keys + bt.begin, sizeof(uint64_t) * n,
+                                                 cudaMemcpyHostToDevice, h->q_up);
+                if (ce == cudaSuccess && !vals_ext)
+                    ce = cudaMemcpyAsync(h->q_vals[q], h->h_vals + bt.begin, sizeof(float) * n,
+                                         cudaMemcpyHostToDevice, h->q_up);
+                return ce;
+            });
         if (e == cudaSuccess) e = cudaEventRecord(h->q_copied[q], h->q_up);
         uploaded = true;
         if (e == cudaSuccess) e = cudaStreamWaitEvent(h->q_stream[q], h->q_copied[q], 0);

@@ -17,9 +17,10 @@
 //      each loading 4 elements of every gathered factor row (16 bytes of
 //      float32, 8 of bf16/fp16), so one warp load moves P = 32/G whole
 //      rows; subgroup g walks the sorted positions [g*G, g*G+G), issuing the
-//      row loads of up to 8 positions back to back, multiplying with packed
-//      f32x2 arithmetic and keeping a running float32 sum while the target
-//      row stays the same (Section 5.1, computing phase);
+//      row loads of up to 4 positions back to back, multiplying with packed
+//      f32x2 arithmetic and keeping a running float32 sum (Kahan-compensated
+//      for 16-bit factors unless disabled) while the target row stays the
+//      same (Section 5.1, computing phase);
 //   4. where a run ends the sum goes either to the warp's own shared-memory
 //      copy of the row (the mode's hottest rows, plain read-modify-write) or
 //      to global memory with one red.global.add.v4.f32 per 16 bytes (every
@@ -27,7 +28,9 @@
 //      build time from a per-mode histogram; when the whole mode fits, every
 //      row is hot. Each CTA adds its warps' copies to global memory once at
 //      exit (Section 5.1's local stash and final merge; the per-mode choice
-//      of Section 5.3 becomes a per-row split).
+//      of Section 5.3 becomes a per-row split). Short modes at R >= 64 reduce
+//      into one of a few private output copies instead (the paper's per-GPC
+//      copies of M), summed by a separate kernel after the launch.
 // The grid is persistent (SM count x resident CTAs); warps stride over the
 // tiles, so the warps running at any moment cover a narrow window of the ALTO
 // order and share factor rows in L2.
