@@ -64,7 +64,7 @@ typedef enum {
     BLCO_ERR_CUDA = 4,        /* a CUDA runtime call or kernel failed */
     BLCO_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
     BLCO_ERR_STATE = 6,       /* handle in the wrong state for the call */
-    BLCO_ERR_UNSUPPORTED = 7  /* a valid request the library does not implement (e.g. a rank outside 8..128) */
+    BLCO_ERR_UNSUPPORTED = 7  /* a valid request the library does not implement (a rank other than 8, 16, 32, 64, 128) */
 } blco_status;
 
 typedef enum { BLCO_F32 = 0, BLCO_BF16 = 1, BLCO_F16 = 2 } blco_dtype;
