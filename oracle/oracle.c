@@ -7,7 +7,9 @@
  * table or helper with the CUDA sources.
  *
  * Everything here is the plain definition, written as loops in the order the
- * paper states it, in double precision, single-threaded:
+ * paper states it, in double precision, single-threaded (orc_mttkrp_rows may
+ * spread independent chunks and rows over OpenMP threads; every sum is still
+ * the same additions in the same order):
  *
  *   orc_alto_layout   Section 4.1, Fig. 6a: the ALTO bit order of a linear
  *                     index (one bit per mode per level, round robin from the
