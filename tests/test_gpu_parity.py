@@ -236,9 +236,18 @@ def test_unreferenced_nonfinite_factor_rows_do_not_leak(nnz):
 
 def test_convert_matches_oracle_rounding():
     x = torch.randn(100_003, device="cuda") * 3
+    # ties, subnormals, overflow and signed zeros as well as ordinary values
+    special = torch.tensor([0.0, -0.0, 1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, 1e-40, -1e-40, 3.4e38, 65520.0,
+                            6.1e-5, 5.9e-8, float("inf"), float("-inf")], device="cuda")
+    x = torch.cat([x, special])
     y = blco.convert(x, torch.bfloat16)
     ref = oracle.bf16_round(x.cpu().numpy())
     assert np.array_equal(y.float().cpu().numpy().view(np.uint32), ref.view(np.uint32))
+    # float16: IEEE binary16 round-to-nearest-even (numpy's cast), incl. overflow to inf
+    h = blco.convert(x, torch.float16)
+    with np.errstate(over="ignore"):
+        ref16 = x.cpu().numpy().astype(np.float16)
+    assert np.array_equal(h.cpu().numpy().view(np.uint16), ref16.view(np.uint16))
 
 
 @pytest.mark.parametrize("nq", [1, 3, 8])
