@@ -479,8 +479,9 @@ cudaError_t launch_gram(const void *A, blco_dtype fdt, int64_t I, int R, double 
     if (e != cudaSuccess || I <= 0) return e;
     const GramShape sh = gram_shape(R);
     const int ny = sh.groups > 1 ? 1 : (sh.nblk + kGramThreads - 1) / kGramThreads;
-    // about two CTAs per SM in total, each over a contiguous range of rows
-    const int64_t ctas_max = std::max<int64_t>(1, (int64_t)sm_count() * 2 / ny);
+    // three CTAs per SM in total (the register limit at 79 registers), each
+    // over a contiguous range of rows
+    const int64_t ctas_max = std::max<int64_t>(1, (int64_t)sm_count() * 3 / ny);
     int64_t rows = (I + ctas_max - 1) / ctas_max;
     rows = std::max<int64_t>(kGramRows, (rows + kGramRows - 1) / kGramRows * kGramRows);
     const int64_t ctas = (I + rows - 1) / rows;
