@@ -184,11 +184,14 @@ def mttkrp_src_sha() -> str:
     return h.hexdigest()
 
 
-def algorithmic_bytes(spec, R: int, fbytes: int, mode: int) -> int:
+def algorithmic_bytes(spec, R: int, fbytes: int, mode: int, rows=None) -> int:
     """Compulsory bytes of one mode-n MTTKRP launch: the key/value stream
-    (8 + 4 bytes per nonzero), every other factor matrix once, the output once."""
-    b = 12 * spec.nnz + 4 * spec.dims[mode] * R
-    for k, d in enumerate(spec.dims):
+    (8 + 4 bytes per nonzero), every other factor matrix once, the output once.
+    With `rows` (rows touched per mode) only the touched rows count: the
+    stricter count."""
+    rows = rows or spec.dims
+    b = 12 * spec.nnz + 4 * rows[mode] * R
+    for k, d in enumerate(rows):
         if k != mode:
             b += d * R * fbytes
     return b
@@ -341,6 +344,8 @@ def run_blco(args, ranks: Ranks):
     torch.cuda.synchronize()
     build_ms = eb0.elapsed_time(eb1)
     info = t.info()
+    # rows each mode's nonzeros touch (for the stricter compulsory-bytes count)
+    touched = [int(torch.unique(coords[:, n]).numel()) for n in range(spec.order)]
     # the same store with plain float32 run sums, for the bf16 comparison
     t_plain = None
     if not args.no_bf16 and not info["streamed"]:
@@ -408,6 +413,7 @@ def run_blco(args, ranks: Ranks):
     per_launch_bytes = bytes_all / spec.order
     per_launch_ms = kms / max(launches, 1)
     achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9 if launches else None
+    touched_bytes = sum(algorithmic_bytes(spec, R, 4, n, touched) for n in range(spec.order)) / spec.order
     traffic = None
     if TRAFFIC_RECORD["mttkrp_src_sha256"] == mttkrp_src_sha() and base_name == DEFAULT_WORKLOAD and not args.nnz:
         traffic = TRAFFIC_RECORD["bytes_per_launch"]
@@ -415,7 +421,10 @@ def run_blco(args, ranks: Ranks):
                 "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                 "kernel": f"k_mttkrp<float,{R},{spec.order - 1}>",
                 "peak_source": peak_src + " (burst copy, MEASURED_PEAKS hbm_gbs)",
-                "algorithmic_bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_ms}
+                "algorithmic_bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_ms,
+                "touched_rows_per_mode": touched,
+                "algorithmic_bytes_touched_rows": touched_bytes,
+                "frac_touched_rows": (touched_bytes / (per_launch_ms / 1e3) / 1e9 / peak) if launches else None}
     if info["streamed"]:
         roofline["note"] = ("streamed store: kernel time measured on the queue streams; the step is bound by "
                             "the host link (see host_link)")
