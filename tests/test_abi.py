@@ -88,3 +88,18 @@ def test_error_object_carries_status_and_message(blco):
     with pytest.raises(blco.BlcoError) as ei:
         blco._check("blco_x", blco.BLCO_ERR_INDEX)
     assert ei.value.status == blco.BLCO_ERR_INDEX and "BLCO_ERR_INDEX" in str(ei.value)
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/blco.h is a C header: it compiles as C99 (no C++ or CUDA
+    types in the signatures) and as C++."""
+    import shutil
+    import subprocess
+
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    for lang, std in (("c", "c99"), ("c++", "c++11")):
+        r = subprocess.run([gcc, "-fsyntax-only", "-x", lang, f"-std={std}", "-Wall", "-Werror", HEADER],
+                           capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
