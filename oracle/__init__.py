@@ -281,4 +281,4 @@ def max_rel_err(M_test, M_ref, S_ref) -> float:
     return float(np.max(diff[~zero] / S_ref[~zero]))
 
 
-from .cpals import cp_als, gram, fit_of  # noqa: E402  (uses the functions above)
+from .cpals import cp_als, gram, fit_of, solve_right, pinv_sym, cholesky_lower, pd_tolerance  # noqa: E402,F401

@@ -415,3 +415,103 @@ def test_cp_als_fit_matches_dense_residual(orc):
     Xh = np.einsum("r,ir,jr,kr->ijk", lam, *A)
     ref = 1 - np.linalg.norm(X - Xh) / np.linalg.norm(X)
     assert abs(fits[-1] - ref) < 1e-10
+
+
+# ------------------------------------------- Algorithm 1: the V^+ of the update
+def _sym_with_spectrum(rng, w):
+    """Q diag(w) Q^T with a random orthogonal Q (QR of a Gaussian matrix)."""
+    Q, _ = np.linalg.qr(rng.standard_normal((len(w), len(w))))
+    return (Q * np.asarray(w, dtype=np.float64)) @ Q.T
+
+
+def _penrose_residuals(V, X):
+    """The four Moore-Penrose conditions of X = V^+, relative to |V| |X| scale."""
+    s = np.linalg.norm(V, 2) * np.linalg.norm(X, 2)
+    return (np.linalg.norm(V @ X @ V - V, 2) / np.linalg.norm(V, 2),
+            np.linalg.norm(X @ V @ X - X, 2) / np.linalg.norm(X, 2),
+            np.linalg.norm((V @ X).T - V @ X, 2) / s,
+            np.linalg.norm((X @ V).T - X @ V, 2) / s)
+
+
+@pytest.mark.parametrize("R,zeros", [(8, 1), (16, 3), (64, 10)])
+def test_singular_v_takes_the_pseudo_inverse_branch(orc, R, zeros):
+    """An exactly rank-deficient symmetric positive semi-definite V: the
+    Cholesky pivot test must reject it (whatever rounding leaves in the zero
+    pivots), and solve_right must return M V^+ with the Penrose conditions
+    holding to rounding."""
+    rng = np.random.default_rng(R)
+    w = np.concatenate([rng.uniform(0.5, 4.0, R - zeros), np.zeros(zeros)])
+    V = _sym_with_spectrum(rng, w)
+    V = 0.5 * (V + V.T)
+    assert orc.cholesky_lower(V) is None
+    X = orc.pinv_sym(V)
+    for r in _penrose_residuals(V, X):
+        assert r <= 1e-12, r
+    # the rank of V^+ is the rank of V: the cut removed exactly the zero eigenvalues
+    assert np.sum(np.abs(np.linalg.eigvalsh(X)) > 1e-8) == R - zeros
+    M = rng.standard_normal((7, R))
+    A, info = orc.solve_right(M, V)
+    assert info == 1
+    np.testing.assert_allclose(A, M @ X, rtol=0, atol=1e-12 * np.abs(M).max() * np.abs(X).max() * R)
+    # A annihilates the null space of V: A v = 0 for V v = 0
+    wv, Qv = np.linalg.eigh(V)
+    null = Qv[:, np.abs(wv) < 1e-10]
+    assert np.abs(A @ null).max() <= 1e-10 * np.abs(A).max()
+
+
+def test_indefinite_v_takes_the_pseudo_inverse_branch(orc):
+    """A symmetric V with a negative eigenvalue is not positive definite: the
+    pseudo-inverse of a nonsingular V is its inverse."""
+    rng = np.random.default_rng(7)
+    V = _sym_with_spectrum(rng, [3.0, 2.0, 1.0, -0.5, 0.25])
+    V = 0.5 * (V + V.T)
+    assert orc.cholesky_lower(V) is None
+    M = rng.standard_normal((4, 5))
+    A, info = orc.solve_right(M, V)
+    assert info == 1
+    # A V = M exactly in exact arithmetic (Gauss-Jordan by hand would do; use the residual)
+    assert np.abs(A @ V - M).max() <= 1e-12 * np.abs(M).max() * np.linalg.cond(V)
+
+
+def test_spd_v_takes_the_cholesky_branch(orc):
+    """A well-conditioned SPD V: Cholesky succeeds, L L^T = V, and the solve
+    gives A V = M; a pivot just at the tolerance is rejected."""
+    rng = np.random.default_rng(8)
+    R = 12
+    V = _sym_with_spectrum(rng, rng.uniform(0.1, 10.0, R))
+    V = 0.5 * (V + V.T)
+    L = orc.cholesky_lower(V)
+    assert L is not None
+    assert np.array_equal(L, np.tril(L)) and np.all(np.diag(L) > 0)
+    np.testing.assert_allclose(L @ L.T, V, rtol=0, atol=1e-13 * np.abs(V).max())
+    M = rng.standard_normal((9, R))
+    A, info = orc.solve_right(M, V)
+    assert info == 0
+    assert np.abs(A @ V - M).max() <= 1e-12 * np.abs(M).max() * np.linalg.cond(V)
+    # the last pivot of diag(1, ..., 1, t) is t: accepted only above R * eps * max diag
+    tol = orc.pd_tolerance(np.eye(R))
+    assert tol == R * np.finfo(np.float64).eps
+    D = np.eye(R)
+    D[-1, -1] = tol
+    assert orc.cholesky_lower(D) is None
+    D[-1, -1] = 2 * tol
+    assert orc.cholesky_lower(D) is not None
+
+
+def test_cp_als_update_uses_solve_right_on_a_singular_problem(orc):
+    """Two identical columns in a factor make every other mode's V singular:
+    the CP-ALS driver must run through the pseudo-inverse branch and still
+    produce finite factors with unit columns."""
+    rng = np.random.default_rng(9)
+    dims = (5, 4, 3)
+    R = 3
+    coords = np.array(list(itertools.product(*[range(d) for d in dims])))
+    vals = rng.random(len(coords))
+    init = [rng.standard_normal((d, R)) for d in dims]
+    for a in init:
+        a[:, 1] = a[:, 0]
+    A, lam, fits = orc.cp_als(coords, vals, dims, init, iters=2)
+    for a in A:
+        assert np.all(np.isfinite(a))
+        norms = np.linalg.norm(a, axis=0)
+        assert np.all((np.abs(norms - 1) < 1e-12) | (norms == 0))
