@@ -76,10 +76,12 @@ typedef struct {
     int32_t n_queues;            /* streaming device queues, 1..8; 0 = 8 */
     int64_t device_budget_bytes; /* cap on this handle's device memory; 0 = none */
     int32_t force_stream;        /* 1 = keep the store in pinned host memory */
-    int32_t plain_sums;          /* 1 = with bf16/fp16 factors, sum each run of
-                                    equal output rows in plain float32 instead of
-                                    Kahan's compensated sum (faster; about one
-                                    rounding per term more within a run) */
+    int32_t compensated_sums;    /* 1 = with bf16/fp16 factors, sum each run of
+                                    equal output rows with Kahan's compensated
+                                    summation instead of plain float32 (about one
+                                    rounding per run instead of one per term; the
+                                    measured errors at the benchmark sizes are the
+                                    same, and the plain sums are 8-10% faster) */
 } blco_build_opts;
 
 typedef struct {
@@ -133,8 +135,8 @@ blco_status blco_build(const uint32_t *coords, const float *vals, int64_t nnz, c
  * Accumulation is float32 (segmented within a warp, then in per-warp
  * shared-memory copies of the mode's hottest rows, then vector reductions to
  * global memory), so the summation order, and the last bits, vary from run
- * to run. With bf16/fp16 factors each in-warp run is Kahan-compensated unless
- * the handle was built with plain_sums.
+ * to run. With bf16/fp16 factors each in-warp run is Kahan-compensated if
+ * the handle was built with compensated_sums.
  * With any host pointer the call returns when `out` is complete; with device
  * pointers only it is asynchronous on `stream`.
  * Errors: BLCO_ERR_ARG, BLCO_ERR_UNSUPPORTED (rank), BLCO_ERR_OOM (staging),
@@ -155,6 +157,31 @@ blco_status blco_mttkrp(blco_handle h, int mode, const void *const *factors, blc
  */
 blco_status blco_mttkrp_all(blco_handle h, const void *const *factors, blco_dtype fdt, int R,
                             float *const *outs, blco_stream stream);
+
+/*
+ * Partial MTTKRP over a contiguous part of the store, for splitting one
+ * MTTKRP across devices or calls. MTTKRP is a sum over nonzeros (Eq. 1),
+ * and the store's parts are independent of one another (Section 4.2: blocks
+ * are processed independently), so the MTTKRP of the whole tensor is the sum
+ * of the partial results of any set of parts that covers the store once; the
+ * paper names distributed memory as future work (Section 8).
+ *   blco_partition: for a store of nnz nonzeros (nnz < 2^32; no handle or
+ *     device needed), bounds[0..nparts] (host) receives nparts contiguous
+ *     ranges of store positions of (nearly) equal size, every bound but the
+ *     last a multiple of 32; bounds[0] = 0, bounds[nparts] = nnz. A range may
+ *     cut a block: a part needs no whole blocks, as every position's block
+ *     is looked up.
+ *   blco_mttkrp_range: out (I_mode x R float32, host or device, overwritten)
+ *     = the mode-`mode` MTTKRP of the nonzeros at store positions
+ *     [begin, end); begin a multiple of 32, 0 <= begin <= end <= nnz. Other
+ *     arguments as blco_mttkrp. The store must be resident on the device
+ *     (BLCO_ERR_STATE for a streamed store).
+ * Errors: BLCO_ERR_ARG, BLCO_ERR_STATE, BLCO_ERR_UNSUPPORTED, BLCO_ERR_OOM,
+ * BLCO_ERR_CUDA.
+ */
+blco_status blco_partition(int64_t nnz, int nparts, int64_t *bounds);
+blco_status blco_mttkrp_range(blco_handle h, int mode, int64_t begin, int64_t end, const void *const *factors,
+                              blco_dtype fdt, int R, float *out, blco_stream stream);
 
 /*
  * CP model at every stored nonzero (Algorithm 1's model, Section 2.2):
@@ -225,9 +252,11 @@ blco_status blco_gram(const void *A, blco_dtype fdt, int64_t I, int R, double *G
  *           product of the other Grams, columns scaled to unit 2-norm
  *   lambda  R float64 output (device): the column norms removed from A
  *   G_out   R x R float64 output (device): Gram of the new A (may be NULL)
- *   info    1 int32 (device): 0 if V was positive definite (Cholesky),
- *           1 if the eigen pseudo-inverse was used
- * R <= 128.
+ *   info    1 int32 (device): 0 if every Cholesky pivot of V exceeded
+ *           R * eps * max_i V_ii (Cholesky solve), 1 otherwise (V numerically
+ *           singular or indefinite: the eigen pseudo-inverse, eigenvalues
+ *           with |w| <= max|w| * R * eps dropped)
+ * R in 1..64; larger ranks return BLCO_ERR_UNSUPPORTED.
  */
 blco_status blco_cpals_update(const double *const *grams, int N, int mode, int R, const float *M,
                               int64_t I, float *A, double *lambda, double *G_out, int32_t *info,
@@ -243,10 +272,15 @@ blco_status blco_cpals_update(const double *const *grams, int N, int mode, int R
  * float32 inverse of V and two per-column vectors) is one fixed array in
  * device memory that every GPU loading libblco.so holds until the process
  * exits. Limits and behaviour:
- *   - R must be in 1..64; larger ranks return BLCO_ERR_ARG.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) and caches it; make that first call before
- *     capturing any stream work.
+ *   - R must be in 1..64; larger ranks return BLCO_ERR_ARG (the size limit
+ *     of the fixed scratch; blco_cpals_update reports the same limit as
+ *     BLCO_ERR_UNSUPPORTED).
+ *   - The first call in a device's context looks up the array's device
+ *     address (cudaGetSymbolAddress) and caches it with the context's id;
+ *     make that first call before capturing any stream work. A context that
+ *     is destroyed and recreated (cudaDeviceReset) may hold the array at
+ *     another address: the next call sees the new context id and looks the
+ *     address up again (again a first call, outside any capture).
  *   - Every call on a device uses the same scratch, which keeps the last
  *     call's contents (the call clears what must start at zero). Calls whose
  *     GPU work overlaps -- on different streams without ordering -- race on

@@ -34,13 +34,14 @@ _DTYPE_CODE = {torch.float32: BLCO_F32, torch.bfloat16: BLCO_BF16, torch.float16
 EXPORTS = ["blco_default_opts", "blco_build", "blco_mttkrp", "blco_mttkrp_all", "blco_cp_fwd", "blco_cp_bwd",
            "blco_values", "blco_perm", "blco_keys", "blco_blocks", "blco_info", "blco_sync", "blco_destroy",
            "blco_last_error", "blco_convert", "blco_gram", "blco_cpals_update", "blco_cpals_fit", "blco_norm2",
-           "blco_profile_enable", "blco_profile_read", "blco_cpals_update_noalloc", "blco_inject_fault"]
+           "blco_profile_enable", "blco_profile_read", "blco_cpals_update_noalloc", "blco_inject_fault",
+           "blco_partition", "blco_mttkrp_range"]
 
 
 class BuildOpts(ctypes.Structure):
     _fields_ = [("max_nnz_per_block", ctypes.c_int64), ("line_bits", ctypes.c_int32), ("n_queues", ctypes.c_int32),
                 ("device_budget_bytes", ctypes.c_int64), ("force_stream", ctypes.c_int32),
-                ("plain_sums", ctypes.c_int32)]
+                ("compensated_sums", ctypes.c_int32)]
 
 
 class ProfileEntry(ctypes.Structure):
@@ -76,6 +77,8 @@ def _load():
         "blco_build": [vp, vp, i64, vp, i32, vp, vp, vp],
         "blco_mttkrp": [vp, i32, vp, i32, i32, vp, vp],
         "blco_mttkrp_all": [vp, vp, i32, i32, vp, vp],
+        "blco_partition": [i64, i32, vp],
+        "blco_mttkrp_range": [vp, i32, i64, i64, vp, i32, i32, vp, vp],
         "blco_cp_fwd": [vp, vp, i32, i32, vp, vp],
         "blco_cp_bwd": [vp, i32, vp, vp, i32, i32, vp, vp],
         "blco_values": [vp, vp, vp],
@@ -201,6 +204,18 @@ def blco_mttkrp_all(h, factors: Sequence, fdt: int, R: int, outs: Sequence, stre
                                                    _stream(stream)))
 
 
+def blco_partition(nnz: int, nparts: int) -> np.ndarray:
+    """Bounds (nparts + 1 store positions) of equal contiguous parts of a store of nnz nonzeros."""
+    b = np.zeros(int(nparts) + 1, dtype=np.int64)
+    _check("blco_partition", _lib.blco_partition(int(nnz), int(nparts), b.ctypes.data))
+    return b
+
+
+def blco_mttkrp_range(h, mode: int, begin: int, end: int, factors: Sequence, fdt: int, R: int, out, stream=None):
+    _check("blco_mttkrp_range", _lib.blco_mttkrp_range(h, int(mode), int(begin), int(end), _ptr_array(factors),
+                                                       int(fdt), int(R), _ptr(out), _stream(stream)))
+
+
 def blco_cp_fwd(h, factors: Sequence, fdt: int, R: int, xhat, stream=None):
     _check("blco_cp_fwd", _lib.blco_cp_fwd(h, _ptr_array(factors), int(fdt), int(R), _ptr(xhat), _stream(stream)))
 
@@ -304,7 +319,7 @@ class Tensor:
     @classmethod
     def build(cls, coords, vals, dims: Sequence[int], *, max_nnz_per_block: int = 0, line_bits: int = 0,
               n_queues: int = 0, device_budget_bytes: int = 0, force_stream: bool = False,
-              plain_sums: bool = False, stream=None) -> "Tensor":
+              compensated_sums: bool = False, stream=None) -> "Tensor":
         o = blco_default_opts()
         if max_nnz_per_block:
             o.max_nnz_per_block = int(max_nnz_per_block)
@@ -314,7 +329,7 @@ class Tensor:
             o.n_queues = int(n_queues)
         o.device_budget_bytes = int(device_budget_bytes)
         o.force_stream = 1 if force_stream else 0
-        o.plain_sums = 1 if plain_sums else 0
+        o.compensated_sums = 1 if compensated_sums else 0
         return cls(blco_build(coords, vals, dims, o, stream), dims)
 
     @property
@@ -443,6 +458,39 @@ class SparseCP(torch.autograd.Function):
             gn = tensor.cp_bwd(n, g, list(factors))
             grads.append(gn if f.dtype == torch.float32 else convert(gn, f.dtype))
         return (None, *grads)
+
+
+def sharded_sum(nnz: int, compute_part, out: torch.Tensor, group=None) -> torch.Tensor:
+    """Data-parallel reduction over the ranks of a torch.distributed group:
+    rank r computes `compute_part(begin, end, out)` for the r-th of `world`
+    equal contiguous parts of the store order (blco_partition), then one
+    all-reduce (sum) of `out` gives every rank the result over all parts.
+    Correct for any function that is a sum over nonzeros, as MTTKRP is
+    (Eq. 1)."""
+    import torch.distributed as dist
+
+    world = dist.get_world_size(group)
+    rank = dist.get_rank(group)
+    b = blco_partition(nnz, world)
+    compute_part(int(b[rank]), int(b[rank + 1]), out)
+    dist.all_reduce(out, op=dist.ReduceOp.SUM, group=group)
+    return out
+
+
+def mttkrp_sharded(tensor: Tensor, mode: int, factors: Sequence, out: Optional[torch.Tensor] = None, group=None,
+                   stream=None) -> torch.Tensor:
+    """Mode-`mode` MTTKRP split over the ranks of a process group, one GPU per
+    rank, each holding the store: every rank runs blco_mttkrp_range on its
+    part, and the I_mode x R partial results are summed by one all-reduce
+    (NCCL on GPUs)."""
+    R = _rank(factors)
+    if out is None:
+        out = torch.empty((tensor.dims[mode], R), dtype=torch.float32, device=factors[(mode + 1) % len(factors)].device)
+
+    def part(begin, end, o):
+        blco_mttkrp_range(tensor.handle, mode, begin, end, factors, _fdt(factors), R, o, stream)
+
+    return sharded_sum(tensor.nnz, part, out, group)
 
 
 def cp_als(tensor: Tensor, factors: List[torch.Tensor], iters: int, tol: float = 0.0, stream=None):

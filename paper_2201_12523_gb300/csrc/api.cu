@@ -87,7 +87,7 @@ struct blco_tensor {
     int nq = 8;
     int64_t budget = 0;
     bool streamed = false;
-    bool compensated = true;  // 16-bit factors: Kahan-compensated run sums
+    bool compensated = false;  // 16-bit factors: Kahan-compensated run sums (build option)
     // store (device when resident, pinned host when streamed)
     uint64_t *d_keys = nullptr;
     float *d_vals = nullptr;
@@ -180,6 +180,7 @@ struct blco_tensor {
         sv.single_block = single_block ? 1 : 0;
         sv.N = L.N;
         for (int n = 0; n < L.N; ++n) {
+            sv.dims[n] = L.dims[n];
             sv.shift[n] = L.shift[n];
             sv.mask[n] = L.width[n] >= 64 ? ~0ull : ((1ull << L.width[n]) - 1ull);
         }
@@ -318,14 +319,22 @@ cudaError_t timed(blco_tensor *h, const char *name, cudaStream_t s, F &&launch) 
 // batches of blocks through the device queues. `vals_ext` replaces the
 // stored values when non-null (a device array in store order).
 template <typename F>
-blco_status over_store(blco_tensor *h, const char *name, const float *vals_ext, cudaStream_t s, F &&launch_fn) {
+blco_status over_store(blco_tensor *h, const char *name, const float *vals_ext, cudaStream_t s, F &&launch_fn,
+                       int64_t range_begin = 0, int64_t range_end = -1) {
+    // name == nullptr: launch_fn times its own launches
     auto launch = [&](const StoreView &sv, cudaStream_t q) {
+        if (!name) return launch_fn(sv, q);
         return timed(h, name, q, [&]() { return launch_fn(sv, q); });
     };
     if (h->nnz == 0) return BLCO_OK;
     if (!h->streamed) {
         StoreView sv = h->view();
         if (vals_ext) sv.vals = vals_ext;
+        if (range_end >= 0) {  // a part of the store (resident stores only)
+            sv.begin = range_begin;
+            sv.end = range_end;
+            if (sv.end <= sv.begin) return BLCO_OK;
+        }
         cudaError_t e = launch(sv, s);
         if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
         return BLCO_OK;
@@ -441,7 +450,7 @@ bool copy_buffer(blco_tensor *h, size_t bytes, float **p) {
 }
 
 blco_status mttkrp_device(blco_tensor *h, int mode, const FactorSet &fs, blco_dtype fdt, int R, float *out,
-                          const float *vals_ext, cudaStream_t s) {
+                          const float *vals_ext, cudaStream_t s, int64_t range_begin = 0, int64_t range_end = -1) {
     const int64_t n = h->L.dims[mode] * (int64_t)R;
     const HotRows hot = hot_for(h, mode, R);
     // short modes: reduce into one private copy per SM, then sum the copies
@@ -456,9 +465,12 @@ blco_status mttkrp_device(blco_tensor *h, int mode, const FactorSet &fs, blco_dt
     }
     cudaError_t e = timed(h, "zero", s, [&]() { return launch_zero(dst, n * oc.n, s); });
     if (e != cudaSuccess) return cuda_fail(e, "zero output");
-    blco_status st = over_store(h, "mttkrp", vals_ext, s, [&](const StoreView &sv, cudaStream_t q) {
-        return launch_mttkrp(sv, fs, fdt, R, mode, hot, dst, oc, h->compensated, q);
-    });
+    blco_status st = over_store(
+        h, "mttkrp", vals_ext, s,
+        [&](const StoreView &sv, cudaStream_t q) {
+            return launch_mttkrp(sv, fs, fdt, R, mode, hot, dst, oc, h->compensated, q);
+        },
+        range_begin, range_end);
     if (st != BLCO_OK || oc.n == 1) return st;
     e = timed(h, "sum_copies", s, [&]() { return launch_sum_copies(dst, oc.n, n, out, s); });
     if (e != cudaSuccess) return cuda_fail(e, "sum of output copies");
@@ -514,7 +526,7 @@ blco_status blco_build(const uint32_t *coords, const float *vals, int64_t nnz, c
         if (opts->n_queues) o.n_queues = opts->n_queues;
         o.device_budget_bytes = opts->device_budget_bytes;
         o.force_stream = opts->force_stream;
-        o.plain_sums = opts->plain_sums;
+        o.compensated_sums = opts->compensated_sums;
     }
     blco_tensor *h = new blco_tensor();
     h->L.N = N;
@@ -531,7 +543,7 @@ blco_status blco_build(const uint32_t *coords, const float *vals, int64_t nnz, c
     h->max_nnz = o.max_nnz_per_block;
     h->nq = o.n_queues;
     h->budget = o.device_budget_bytes;
-    h->compensated = o.plain_sums == 0;
+    h->compensated = o.compensated_sums != 0;
     if (cudaGetDevice(&h->device) != cudaSuccess) {
         cudaGetLastError();
         delete h;
@@ -727,6 +739,58 @@ blco_status blco_mttkrp(blco_handle h, int mode, const void *const *factors, blc
     return BLCO_OK;
 }
 
+blco_status blco_partition(int64_t nnz, int nparts, int64_t *bounds) {
+    g_err.clear();
+    if (!bounds) return fail(BLCO_ERR_ARG, "bounds is NULL");
+    if (nparts < 1) return fail(BLCO_ERR_ARG, "nparts must be >= 1");
+    if (nnz < 0 || nnz >= ((int64_t)1 << 32)) return fail(BLCO_ERR_ARG, "nnz must be in 0..2^32-1");
+    // equal shares of the store order, cut at multiples of 32 positions
+    bounds[0] = 0;
+    for (int i = 1; i < nparts; ++i) {
+        const int64_t b = nnz * i / nparts / 32 * 32;  // nnz < 2^32, i < 2^31: no overflow
+        bounds[i] = std::max(bounds[i - 1], b);
+    }
+    bounds[nparts] = nnz;
+    return BLCO_OK;
+}
+
+blco_status blco_mttkrp_range(blco_handle h, int mode, int64_t begin, int64_t end, const void *const *factors,
+                              blco_dtype fdt, int R, float *out, blco_stream stream) {
+    g_err.clear();
+    blco_status st = check_common(h, fdt, R);
+    if (st != BLCO_OK) return st;
+    if (h->streamed) return fail(BLCO_ERR_STATE, "blco_mttkrp_range needs a store resident on the device");
+    if (mode < 0 || mode >= h->L.N) return fail(BLCO_ERR_ARG, "mode out of range");
+    if (begin < 0 || end < begin || end > h->nnz) return fail(BLCO_ERR_ARG, "range outside the store");
+    if (begin % 32 != 0) return fail(BLCO_ERR_ARG, "begin must be a multiple of 32");
+    if (!out) return fail(BLCO_ERR_ARG, "out is NULL");
+    if (reinterpret_cast<uintptr_t>(out) & 15) return fail(BLCO_ERR_ARG, "out is not 16-byte aligned");
+    std::string why;
+    if (!check_factors(h, factors, mode, why)) return fail(BLCO_ERR_ARG, why);
+    DeviceGuard g(h->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const bool host_out = !is_device_ptr(out);
+    const size_t out_bytes = (size_t)h->L.dims[mode] * R * sizeof(float);
+    Staged sf;
+    void *dout = nullptr;
+    st = stage_factors(h, factors, mode, fdt, R, host_out ? out_bytes : 0, sf, &dout, s);
+    if (st != BLCO_OK) return st;
+    float *o = host_out ? static_cast<float *>(dout) : out;
+    st = mttkrp_device(h, mode, sf.fs, fdt, R, o, nullptr, s, begin, end);
+    if (st != BLCO_OK) return st;
+    if (host_out) {
+        cudaError_t e = cudaMemcpyAsync(out, o, out_bytes, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "result download");
+    } else if (sf.used > 0) {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "mttkrp_range");
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "mttkrp_range");
+    return BLCO_OK;
+}
+
 // Streams and events of the pipelined host-argument path.
 cudaError_t copy_streams(blco_tensor *h) {
     if (h->up) return cudaSuccess;
@@ -739,6 +803,66 @@ cudaError_t copy_streams(blco_tensor *h) {
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_out[n], cudaEventDisableTiming);
     }
     return e;
+}
+
+// All-mode MTTKRP of a streamed store (Section 4.2): every batch of blocks
+// crosses the host link once per call, and while it sits in its queue's
+// reservation the kernels of all requested modes run on it, one after
+// another on the queue's stream. Host arguments are staged in the
+// workspace: factors uploaded on `s` first, results downloaded at the end.
+// Short modes accumulate straight into their outputs here (no private
+// copies: their buffer holds one mode at a time).
+static blco_status mttkrp_all_streamed(blco_tensor *h, FactorSet fs, const bool *host_in, const bool *host_out,
+                                       const size_t *in_off, const size_t *out_off, size_t total, blco_dtype fdt, int R,
+                                       float *const *outs, cudaStream_t s) {
+    const int N = h->L.N;
+    char *base = nullptr;
+    if (total > 0) {
+        void *p = nullptr;
+        cudaError_t e = h->workspace(total, &p);
+        if (e != cudaSuccess) return cuda_fail(e, "staging workspace");
+        base = static_cast<char *>(p);
+    }
+    float *dst[MAXN] = {};
+    HotRows hot[MAXN];
+    for (int k = 0; k < N; ++k) {
+        if (!host_in[k]) continue;
+        cudaError_t e = cudaMemcpyAsync(base + in_off[k], fs.ptr[k], (size_t)h->L.dims[k] * R * dtype_size(fdt),
+                                        cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(e, "factor upload");
+        fs.ptr[k] = base + in_off[k];
+    }
+    for (int n = 0; n < N; ++n) {
+        if (!outs[n]) continue;
+        dst[n] = host_out[n] ? reinterpret_cast<float *>(base + out_off[n]) : outs[n];
+        hot[n] = hot_for(h, n, R);
+        const int64_t cnt = h->L.dims[n] * (int64_t)R;
+        cudaError_t e = timed(h, "zero", s, [&]() { return launch_zero(dst[n], cnt, s); });
+        if (e != cudaSuccess) return cuda_fail(e, "zero output");
+    }
+    const OutCopies one;
+    blco_status st = over_store(h, nullptr, nullptr, s, [&](const StoreView &sv, cudaStream_t q) {
+        for (int n = 0; n < N; ++n) {
+            if (!outs[n]) continue;
+            cudaError_t e = timed(h, "mttkrp", q, [&]() {
+                return launch_mttkrp(sv, fs, fdt, R, n, hot[n], dst[n], one, h->compensated, q);
+            });
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    });
+    if (st != BLCO_OK) return st;
+    for (int n = 0; n < N; ++n) {
+        if (!outs[n] || !host_out[n]) continue;
+        cudaError_t e = cudaMemcpyAsync(outs[n], dst[n], (size_t)h->L.dims[n] * R * sizeof(float),
+                                        cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return cuda_fail(e, "result download");
+    }
+    if (total > 0) {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "mttkrp_all");
+    }
+    return BLCO_OK;
 }
 
 blco_status blco_mttkrp_all(blco_handle h, const void *const *factors, blco_dtype fdt, int R, float *const *outs,
@@ -773,6 +897,7 @@ blco_status blco_mttkrp_all(blco_handle h, const void *const *factors, blco_dtyp
     }
     FactorSet fs;
     for (int k = 0; k < MAXN; ++k) fs.ptr[k] = k < N ? factors[k] : nullptr;
+    if (h->streamed) return mttkrp_all_streamed(h, fs, host_in, host_out, in_off, out_off, total, fdt, R, outs, s);
     if (total == 0) {  // device arguments: the modes one after another on s
         for (int n = 0; n < N; ++n) {
             if (!outs[n]) continue;

@@ -193,13 +193,22 @@ __global__ void __launch_bounds__(256) k_solve_small(const GramPtrs gp, int N, i
         V[p] = v;
         L[p] = v;
     }
-    if (tid == 0) ok = 1;
+    __shared__ double pd_tol;
+    if (tid == 0) {
+        ok = 1;
+        // smallest pivot accepted as positive: R * eps * max_i V_ii; at or
+        // below it V is treated as not positive definite (numerically
+        // singular or indefinite) and the pseudo-inverse is used
+        double m = 0.0;
+        for (int i = 0; i < R; ++i) m = fmax(m, V[i * R + i]);
+        pd_tol = (double)R * 2.220446049250313e-16 * m;
+    }
     __syncthreads();
     // Cholesky, right-looking, in L (lower triangle)
     for (int j = 0; j < R; ++j) {
         if (tid == 0) {
             const double d = L[j * R + j];
-            if (!(d > 0.0)) ok = 0;
+            if (!(d > pd_tol)) ok = 0;
             L[j * R + j] = d > 0.0 ? sqrt(d) : 1.0;
         }
         __syncthreads();
@@ -598,24 +607,64 @@ constexpr size_t kNoAllocScratchBytes = kNoAllocInvOff + sizeof(float) * kNoAllo
 // Shared by every call on a device; holds the previous call's contents.
 static __device__ __align__(256) unsigned char g_update_scratch[kNoAllocScratchBytes];
 
-std::mutex g_scratch_mutex;
-void *g_scratch_addr[64] = {};
+// The array's device address is looked up once per device and context
+// (cudaGetSymbolAddress: the host-side name of the array is not a device
+// address) and cached with the id of the context it belongs to. A context
+// that is destroyed and recreated (cudaDeviceReset) reloads the module,
+// possibly at another address; its new id makes the next call look the
+// address up again instead of using a stale one.
+typedef int (*CtxGetCurrentFn)(void **);
+typedef int (*CtxGetIdFn)(void *, unsigned long long *);
 
-// Device address of g_update_scratch on the current device, looked up once
-// per device (the host-side name of the array is not a device address).
+struct ScratchCache {
+    unsigned long long ctx_id = 0;  // 0: nothing cached
+    void *addr = nullptr;
+};
+
+std::mutex g_scratch_mutex;
+ScratchCache g_scratch[64];
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
+bool g_driver_looked_up = false;
+
+// Id of the calling thread's current context, 0 if unknown.
+unsigned long long current_ctx_id() {
+    if (!g_driver_looked_up) {
+        g_driver_looked_up = true;
+        void *f = nullptr, *g = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &g, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+            g_ctx_current = reinterpret_cast<CtxGetCurrentFn>(f);
+            g_ctx_id = reinterpret_cast<CtxGetIdFn>(g);
+        }
+        cudaGetLastError();
+    }
+    if (!g_ctx_current || !g_ctx_id) return 0;
+    void *ctx = nullptr;
+    unsigned long long id = 0;
+    if (g_ctx_current(&ctx) != 0 || !ctx || g_ctx_id(ctx, &id) != 0) return 0;
+    return id;
+}
+
+// Device address of g_update_scratch in the current device's context.
 cudaError_t update_scratch(unsigned char **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (!g_scratch_addr[dev]) {
+    const unsigned long long id = current_ctx_id();
+    ScratchCache &c = g_scratch[dev];
+    if (id == 0 || c.ctx_id != id) {
         void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_update_scratch);
+        e = cudaGetSymbolAddress(&p, g_update_scratch);  // also makes the primary context current
         if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = p;
+        c.addr = p;
+        c.ctx_id = current_ctx_id();  // 0 (no driver entry points): look up again on every call
     }
-    *out = static_cast<unsigned char *>(g_scratch_addr[dev]);
+    *out = static_cast<unsigned char *>(c.addr);
     return cudaSuccess;
 }
 

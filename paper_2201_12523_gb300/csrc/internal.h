@@ -47,6 +47,7 @@ struct StoreView {
     const uint32_t *bbase;       // nblocks x MAXN: block high bits << field width
     int single_block;            // 1: one block with zero high bits (no lookups)
     int N;
+    int64_t dims[MAXN];
     int shift[MAXN];
     uint64_t mask[MAXN];
 };

@@ -88,7 +88,7 @@ struct KParams {
     const uint32_t *hot_rows;
     int kw;
     int hot_dense;
-    int log2nb;  // 2^log2nb buckets of 8 hot row ids (-1: no table)
+    int log2nb;  // 2^log2nb buckets of two hot row ids (-1: no table)
 };
 
 // ---------------------------------------------------------------- helpers
@@ -266,19 +266,19 @@ __host__ __device__ constexpr int gather_slots() {
 }
 
 // Byte offsets of the MTTKRP kernel's shared-memory sections, each rounded
-// up to 16 bytes (the warp-tier updates and the bucket reads are 16-byte
-// vector accesses). Used by the kernel and by its launcher.
+// up to 16 bytes: each warp's staging of its tile, the per-warp copies of
+// the hot rows (kw rows plus one spare row that takes the padded lanes of a
+// ragged tile and is never merged), and the table of hot row ids (nb buckets
+// of two (row, slot) pairs, 16 bytes each, read with one vector load).
 struct SmemLayout {
-    size_t wacc, bkey, bslot, bfill, total;
+    size_t wacc, table, total;
 };
 __host__ __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 __host__ __device__ __forceinline__ SmemLayout smem_layout(size_t stage_bytes, int kw, int R, int nb) {
     SmemLayout L;
     L.wacc = align16(stage_bytes * kWarps);
-    L.bkey = align16(L.wacc + (size_t)kWarps * kw * R * sizeof(float));
-    L.bslot = align16(L.bkey + (size_t)nb * 8 * sizeof(uint32_t));
-    L.bfill = align16(L.bslot + (size_t)nb * 8 * sizeof(uint16_t));
-    L.total = align16(L.bfill + (size_t)nb * sizeof(int));
+    L.table = align16(L.wacc + (size_t)kWarps * (kw + 1) * R * sizeof(float));
+    L.total = align16(L.table + (size_t)nb * sizeof(uint4));
     return L;
 }
 
@@ -304,11 +304,13 @@ struct Stage {
 // -------------------------------------------------------------------------
 // Resident CTAs per SM the register budget is sized for (80 registers for
 // 3, 128 for 2). Measured on GB300: the MTTKRP kernel is fastest with 3 up
-// to R = 32 (also with 3 gathered modes: -10% at 4 modes) and with 2 at
-// R = 64; the CP-model kernel keeps 2 where it gathers 3 or more rows.
+// to R = 32 (also with 3 gathered modes: -10% at 4 modes) and at R = 64 with
+// two gathered modes (82 registers, hence 2 CTAs, made the planted 3-mode
+// R = 64 adjoint 15% slower); more gathered rows at R = 64 keep 2. The
+// CP-model kernel keeps 2 where it gathers 3 or more rows.
 template <int R, int NG>
 __host__ __device__ constexpr int mttkrp_min_ctas() {
-    return (R >= 64 || NG == 0) ? 2 : 3;
+    return (NG == 0 || R > 64 || (R == 64 && NG > 2)) ? 2 : 3;
 }
 template <int R, int NG>
 __host__ __device__ constexpr int cp_min_ctas() {
@@ -327,45 +329,38 @@ __global__ void __launch_bounds__(kThreads, mttkrp_min_ctas<R, NG>()) k_mttkrp(c
 
     extern __shared__ __align__(16) unsigned char smem[];
     const int kw = p.kw;  // warp tier: the hottest rows, one private copy per warp
-    const int nb = p.log2nb >= 0 ? (1 << p.log2nb) : 0;  // buckets of 8 row ids
+    const int nb = p.log2nb >= 0 ? (1 << p.log2nb) : 0;  // buckets of two row ids
     const SmemLayout L = smem_layout(sizeof(MStage<NG>), kw, R, nb);
     MStage<NG> *stage = reinterpret_cast<MStage<NG> *>(smem);
     float *wacc_all = reinterpret_cast<float *>(smem + L.wacc);
-    uint32_t *bkey = reinterpret_cast<uint32_t *>(smem + L.bkey);
-    uint16_t *bslot = reinterpret_cast<uint16_t *>(smem + L.bslot);
-    int *bfill = reinterpret_cast<int *>(smem + L.bfill);
+    uint4 *table = reinterpret_cast<uint4 *>(smem + L.table);
 
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
     const int g = lane / G;
     const int c = lane % G;
     MStage<NG> &st = stage[wid];
-    float *wacc = wacc_all + (size_t)wid * kw * R;
+    float *wacc = wacc_all + (size_t)wid * (kw + 1) * R;
     const int ng = n_gather<NG>(p);
     float *const outp = p.out + (p.ncopies > 1 ? (size_t)(blockIdx.x % p.ncopies) * p.copy_stride : 0);
 
-    // --- zero the accumulators, build the hot-row table: one hash, buckets
-    // of 8 row ids filled in order of decreasing count by warp 0; a row that
-    // finds its bucket full stays off chip (it is then simply a cold row)
-    for (int i = threadIdx.x; i < kWarps * kw * R; i += kThreads) wacc_all[i] = 0.f;
-    for (int i = threadIdx.x; i < nb * 8; i += kThreads) bkey[i] = kNoRow;
-    for (int i = threadIdx.x; i < nb; i += kThreads) bfill[i] = 0;
+    // --- zero the accumulators; thread 0 fills the hot-row table in order of
+    // decreasing count (one hash, buckets of two (row, slot) pairs; a row that
+    // finds its bucket full stays off chip and is simply a cold row)
+    for (int i = threadIdx.x; i < kWarps * (kw + 1) * R; i += kThreads) wacc_all[i] = 0.f;
+    for (int i = threadIdx.x; i < nb; i += kThreads) table[i] = make_uint4(kNoRow, 0u, kNoRow, 0u);
     __syncthreads();
-    if (nb > 0 && wid == 0) {
-        for (int i0 = 0; i0 < kw; i0 += 32) {
-            const int i = i0 + lane;
-            const bool in = i < kw;
-            const uint32_t row = in ? __ldg(p.hot_rows + i) : kNoRow;
-            const uint32_t b = in ? hot_hash(row, p.log2nb) : 0xFFFFFFFFu;
-            const unsigned same = __match_any_sync(kFull, b);
-            const int at = bfill[in ? b : 0] + __popc(same & ((1u << lane) - 1u));
-            __syncwarp();
-            if (in && at < 8) {
-                bkey[b * 8 + at] = row;
-                bslot[b * 8 + at] = (uint16_t)i;
+    if (nb > 0 && threadIdx.x == 0) {
+        for (int i = 0; i < kw; ++i) {
+            const uint32_t row = __ldg(p.hot_rows + i);
+            uint4 &bk = table[hot_hash(row, p.log2nb)];
+            if (bk.x == kNoRow) {
+                bk.x = row;
+                bk.y = (uint32_t)i;
+            } else if (bk.z == kNoRow) {
+                bk.z = row;
+                bk.w = (uint32_t)i;
             }
-            if (in && lane == __ffs(same) - 1) bfill[b] += __popc(same);
-            __syncwarp();
         }
     }
     __syncthreads();
@@ -397,8 +392,8 @@ __global__ void __launch_bounds__(kThreads, mttkrp_min_ctas<R, NG>()) k_mttkrp(c
         }
 
         // Lanes past the end of the store (the ragged last tile) take lane 0's
-        // nonzero with value 0: they join its run and add exact zeros (for
-        // finite factors), so no later step needs a per-lane validity test.
+        // key with value 0, so that every row they read exists; below they
+        // form a group of their own, whose sum is never stored.
         {
             const uint64_t key0 = __shfl_sync(kFull, key, 0);
             if (!valid) {
@@ -419,27 +414,24 @@ __global__ void __launch_bounds__(kThreads, mttkrp_min_ctas<R, NG>()) k_mttkrp(c
             for (int q = 0; q < NS; ++q)
                 if (q < ng) o[q] += __ldg(bb + p.gat[q].mode);
         }
-        // --- on-chip slot of this lane's row (one lookup per nonzero: two
-        // 16-byte shared loads of the row's bucket, no probing loop)
+        // --- on-chip slot of this lane's row (one lookup per nonzero: one
+        // 16-byte shared load of the row's bucket, no probing loop)
         int slot = -1;
         {
             if (p.hot_dense) {
                 slot = (int)t;
             } else if (nb > 0) {
-                const uint32_t b = hot_hash(t, p.log2nb);
-                const uint4 k0 = *reinterpret_cast<const uint4 *>(bkey + b * 8);
-                const uint4 k1 = *reinterpret_cast<const uint4 *>(bkey + b * 8 + 4);
-                int e = -1;
-                e = (k1.w == t) ? 7 : e;
-                e = (k1.z == t) ? 6 : e;
-                e = (k1.y == t) ? 5 : e;
-                e = (k1.x == t) ? 4 : e;
-                e = (k0.w == t) ? 3 : e;
-                e = (k0.z == t) ? 2 : e;
-                e = (k0.y == t) ? 1 : e;
-                e = (k0.x == t) ? 0 : e;
-                if (e >= 0) slot = (int)bslot[b * 8 + e];
+                const uint4 bk = table[hot_hash(t, p.log2nb)];
+                slot = (bk.x == t) ? (int)bk.y : ((bk.z == t) ? (int)bk.w : -1);
             }
+        }
+        // padded lanes: a group of their own (kNoRow is no row), which the
+        // sort places after every real nonzero, summed into the warp's spare
+        // slot kw, which is never merged into the output -- so a factor row
+        // holding Inf never meets a padded lane's 0
+        if (!valid) {
+            t = kNoRow;
+            slot = kw;
         }
 
         // --- group equal target rows; counting sort of the groups by leader
@@ -477,9 +469,12 @@ __global__ void __launch_bounds__(kThreads, mttkrp_min_ctas<R, NG>()) k_mttkrp(c
 #pragma unroll
         for (int c0 = 0; c0 < STEPS; c0 += CH) {
             f2 pr[CH][H];
+            uint32_t ridx[CH][NS];
 #pragma unroll
             for (int j = 0; j < CH; ++j) {
                 const float v = st.val[g * STEPS + c0 + j];
+#pragma unroll
+                for (int q = 0; q < NS; ++q) ridx[j][q] = (q < ng) ? st.idx[q][g * STEPS + c0 + j] : 0u;
                 const f2 vv = pack2(v, v);
 #pragma unroll
                 for (int h = 0; h < H; ++h) pr[j][h] = vv;
@@ -490,7 +485,7 @@ __global__ void __launch_bounds__(kThreads, mttkrp_min_ctas<R, NG>()) k_mttkrp(c
                     f2 f[CH][H];
 #pragma unroll
                     for (int j = 0; j < CH; ++j)
-                        load_slice<T, VEC>(p.gat[q].ptr, (size_t)st.idx[q][g * STEPS + c0 + j] * R + c * VEC, f[j]);
+                        load_slice<T, VEC>(p.gat[q].ptr, (size_t)ridx[j][q] * R + c * VEC, f[j]);
 #pragma unroll
                     for (int j = 0; j < CH; ++j)
 #pragma unroll
@@ -563,7 +558,7 @@ __global__ void __launch_bounds__(kThreads, mttkrp_min_ctas<R, NG>()) k_mttkrp(c
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
         for (int w = 0; w < kWarps; ++w) {
-            const float4 x = *reinterpret_cast<const float4 *>(wacc_all + ((size_t)w * kw + sl) * R + q * 4);
+            const float4 x = *reinterpret_cast<const float4 *>(wacc_all + ((size_t)w * (kw + 1) + sl) * R + q * 4);
             v.x += x.x;
             v.y += x.y;
             v.z += x.z;
@@ -786,9 +781,8 @@ cudaError_t mttkrp_as(const StoreView &sv, const FactorSet &fs, int R, int mode,
     } else if (hot.count > 0) {
         p.hot_rows = hot.rows;
         p.kw = hot.count < warp_tier_rows(R) ? hot.count : warp_tier_rows(R);
-        // buckets of 8 at an average load of at most 4 rows
         int l = 0;
-        while ((1 << l) * 4 < p.kw) ++l;
+        while ((1 << l) < 2 * p.kw) ++l;
         p.log2nb = l;
     }
     // float32 factors: plain run sums only; 16-bit factors: compensated

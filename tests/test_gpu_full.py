@@ -114,7 +114,7 @@ def test_zipf4d_500M_fp32_and_bf16():
     torch.cuda.empty_cache()
     _tick("generated")
     t = blco.Tensor.build(coords, vals, spec.dims)
-    tp = blco.Tensor.build(coords, vals, spec.dims, plain_sums=True)
+    tp = blco.Tensor.build(coords, vals, spec.dims, compensated_sums=True)
     c, v = _host(coords, vals)
     del coords, vals
     _tick("built")
@@ -127,10 +127,10 @@ def test_zipf4d_500M_fp32_and_bf16():
     A16 = [blco.convert(a, torch.bfloat16) for a in A]
     e16 = _sampled_mttkrp(t, spec.dims, A16, rows, ref32, BF16_TOL, "zipf4d bf16 vs unrounded")
     e16r = _sampled_mttkrp(t, spec.dims, A16, rows, ref16, FP32_TOL, "zipf4d bf16 vs rounded")
-    e16p = _sampled_mttkrp(tp, spec.dims, A16, rows, ref16, FP32_TOL, "zipf4d bf16 plain sums vs rounded")
+    e16p = _sampled_mttkrp(tp, spec.dims, A16, rows, ref16, FP32_TOL, "zipf4d bf16 compensated sums vs rounded")
     print("per-mode max rel err f32:", [f"{e:.2e}" for e in e32], "bf16:", [f"{e:.2e}" for e in e16],
-          "bf16 (rounded factors), compensated runs:", [f"{e:.2e}" for e in e16r],
-          "plain runs:", [f"{e:.2e}" for e in e16p])
+          "bf16 (rounded factors), plain runs:", [f"{e:.2e}" for e in e16r],
+          "compensated runs:", [f"{e:.2e}" for e in e16p])
     _tick("done")
 
 
@@ -203,13 +203,23 @@ def test_cp_planted_200M_fwd_bwd_and_als():
     g = synth.noise(len(perm), 1.0, spec.seed + 7, device="cuda")
     g64 = g.cpu().numpy().astype(np.float64)
     cstore = c[perm]
+    A16 = [blco.convert(a, torch.bfloat16) for a in A]
+    Ar = rounded16(A, torch.bfloat16)
     for n in range(3):
         out = t.cp_bwd(n, g, A)
         rows = _rows_to_check(cstore[:, n], spec.dims[n], rng)
         M, S = oracle.mttkrp_rows(cstore, g64, spec.dims, Af, n, rows)
-        err = oracle.max_rel_err(out[torch.from_numpy(rows).cuda()].cpu().numpy(), M, S)
+        sel = torch.from_numpy(rows).cuda()
+        err = oracle.max_rel_err(out[sel].cpu().numpy(), M, S)
         print(f"cp_bwd mode {n}: max rel err {err:.3e}")
         assert err <= FP32_TOL
+        # bf16 factors (float32 accumulation): against the unrounded and the rounded factors
+        out16 = t.cp_bwd(n, g, A16)[sel].cpu().numpy()
+        e_unr = oracle.max_rel_err(out16, M, S)
+        Mr, Sr = oracle.mttkrp_rows(cstore, g64, spec.dims, Ar, n, rows)
+        e_r = oracle.max_rel_err(out16, Mr, Sr)
+        print(f"cp_bwd bf16 mode {n}: max rel err {e_unr:.3e} (unrounded factors), {e_r:.3e} (rounded)")
+        assert e_unr <= BF16_TOL and e_r <= FP32_TOL
     del cstore
     _tick("forward and adjoint checked")
     # 20 CP-ALS sweeps (MTTKRP in FP32, R x R algebra in FP64)

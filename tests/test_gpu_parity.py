@@ -190,18 +190,18 @@ def test_mttkrp_16bit_factors(dtype):
 def test_16bit_run_sum_is_compensated(dtype, R):
     """Eight nonzeros of one output row, the first 1.0 and seven of 2^-25,
     all within one subgroup's run (factors of ones are exact in 16 bits).
-    The compensated run sum returns the float32 nearest the exact
-    1 + 1.75 * 2^-23, i.e. 1 + 2^-22; with plain_sums the terms are added one
-    by one in float32 and each tiny one is lost: 1.0."""
+    With compensated_sums the run sum returns the float32 nearest the exact
+    1 + 1.75 * 2^-23, i.e. 1 + 2^-22; with the default plain float32 sums the
+    terms are added one by one and each tiny one is lost: 1.0."""
     dims = (4, 8, 2)
     c = np.array([[1, j, 0] for j in range(8)], dtype=np.int32)  # ALTO order = j order
     v = np.array([1.0] + [2.0 ** -25] * 7, dtype=np.float32)
     A = [blco.convert(torch.ones((d, R), device="cuda"), dtype) for d in dims]
-    for plain, want in [(False, 1.0 + 2.0 ** -22), (True, 1.0)]:
-        t = blco.Tensor.build(torch.from_numpy(c).cuda(), torch.from_numpy(v).cuda(), dims, plain_sums=plain)
+    for comp, want in [(True, 1.0 + 2.0 ** -22), (False, 1.0)]:
+        t = blco.Tensor.build(torch.from_numpy(c).cuda(), torch.from_numpy(v).cuda(), dims, compensated_sums=comp)
         assert np.array_equal(t.perm(), np.arange(8))
         out = t.mttkrp(0, A).cpu().numpy()
-        assert np.all(out[1] == np.float32(want)), (plain, out[1])
+        assert np.all(out[1] == np.float32(want)), (comp, out[1])
         assert np.all(out[[0, 2, 3]] == 0.0)
 
 
@@ -234,6 +234,38 @@ def test_unreferenced_nonfinite_factor_rows_do_not_leak(nnz):
         assert np.all(out[np.setdiff1d(np.arange(dims[n]), used)] == 0.0)
 
 
+@pytest.mark.parametrize("nnz", [33, 1000, 4099])
+def test_referenced_infinite_factor_row_in_the_ragged_tail(nnz):
+    """The first nonzero of the last (ragged) tile references a factor row
+    holding +Inf. The oracle's sums are then +Inf wherever that row enters
+    (all factors positive, so no Inf - Inf): lanes past the end of the store
+    must add nothing there, so the library gives +Inf too, not the NaN that
+    0 * Inf would leave."""
+    rng = np.random.default_rng(nnz + 7)
+    dims = (50, 40, 30)
+    c = np.unique(np.stack([rng.integers(0, d, nnz + 200) for d in dims], 1), axis=0)[:nnz]
+    rng.shuffle(c)
+    vals = (rng.random(len(c)) + 0.5).astype(np.float32)
+    R = 16
+    hostA = [(rng.random((d, R)) + 0.5).astype(np.float32) for d in dims]
+    t = blco.Tensor.build(torch.from_numpy(c.astype(np.int32)).cuda(), torch.from_numpy(vals).cuda(), dims)
+    last = (len(c) - 1) // 32 * 32  # store position of the last tile's first lane
+    j = int(t.perm()[last])
+    hostA[1][c[j, 1]] = np.inf
+    A = [torch.from_numpy(a).cuda() for a in hostA]
+    Af = [a.astype(np.float64) for a in hostA]
+    v64 = vals.astype(np.float64)
+    for n in range(3):
+        out = t.mttkrp(n, A).cpu().numpy()
+        M, S = oracle.mttkrp(c, v64, dims, Af, n)
+        inf = np.isinf(M)
+        assert not np.isnan(M).any()
+        assert (n == 1) == (not inf.any())
+        assert np.array_equal(np.isposinf(out), inf) and not np.isnan(out).any()
+        fin = ~inf
+        assert oracle.max_rel_err(out[fin], M[fin], S[fin]) <= FP32_TOL
+
+
 def test_convert_matches_oracle_rounding():
     x = torch.randn(100_003, device="cuda") * 3
     # ties, subnormals, overflow and signed zeros as well as ordinary values
@@ -259,6 +291,37 @@ def test_streamed_store_matches(nq):
     assert info["streamed"] and info["nblocks"] > 30
     check_mttkrp_all(t, coords, vals, A, spec.dims)
     _store_equal(t, coords, vals, spec.dims, 64, 4000)
+
+
+@pytest.mark.parametrize("nq", [1, 3])
+def test_streamed_all_mode_uploads_each_batch_once(nq):
+    """All-mode MTTKRP of a streamed store: each batch of blocks crosses the
+    host link once per call (Section 4.2's queues), and every mode's kernel
+    runs on it while it is resident; the results match the oracle, also for
+    a short R = 64 mode and with bf16 factors."""
+    spec = synth.small(3, 150_000, (1 << 24, 1 << 20, 1 << 16, 1 << 12, 1 << 8))
+    coords, vals, _ = make(spec)
+    t = blco.Tensor.build(coords, vals, spec.dims, force_stream=True, max_nnz_per_block=4000, n_queues=nq)
+    c = coords.cpu().numpy()
+    v = vals.cpu().numpy().astype(np.float64)
+    for R, dt in ((16, torch.float32), (64, torch.float32), (32, torch.bfloat16)):
+        A = synth.factors(spec, rank=R, device="cuda", dist="normal")
+        F = A if dt == torch.float32 else [blco.convert(a, dt) for a in A]
+        Aref = to_np64(A) if dt == torch.float32 else rounded16(A, dt)
+        blco.blco_profile_enable(t.handle, True)
+        t.mttkrp(0, F)
+        one = blco.blco_profile_read(t.handle)
+        outs = t.mttkrp_all(F)
+        torch.cuda.synchronize()
+        allm = blco.blco_profile_read(t.handle)
+        blco.blco_profile_enable(t.handle, False)
+        batches = one["upload"][0]
+        assert batches > 1
+        assert allm["upload"][0] == batches
+        assert allm["mttkrp"][0] == batches * 5
+        for n in range(5):
+            M, S = oracle.mttkrp(c, v, spec.dims, Aref, n)
+            assert oracle.max_rel_err(outs[n].cpu().numpy(), M, S) <= FP32_TOL, (R, dt, n)
 
 
 @pytest.mark.parametrize("streamed", [False, True])
@@ -324,6 +387,46 @@ def test_mttkrp_all_mixed_host_and_device_arguments(streamed):
             assert oracle.max_rel_err(got, M, S) <= FP32_TOL, (rep, n)
 
 
+@pytest.mark.parametrize("parts", [2, 3, 7])
+def test_partitioned_mttkrp_sums_to_the_full_result(parts):
+    """The store cut into equal contiguous parts (blco_partition), each
+    part's MTTKRP computed alone (blco_mttkrp_range, one after another on
+    one GPU, as the ranks of a partitioned run would), and the parts summed:
+    the oracle's MTTKRP of the whole tensor; every part alone matches the
+    oracle on that part's nonzeros. A blocked 5-mode store, so that parts
+    cut blocks."""
+    spec = synth.small(3, 50_000, (1 << 24, 1 << 20, 1 << 16, 1 << 12, 1 << 8))
+    coords, vals, A = make(spec)
+    t = blco.Tensor.build(coords, vals, spec.dims, max_nnz_per_block=3000)
+    assert t.info()["nblocks"] > parts
+    b = blco.blco_partition(spec.nnz, parts)
+    cs = coords.cpu().numpy()[t.perm()]
+    vs = t.values().cpu().numpy().astype(np.float64)
+    Af = to_np64(A)
+    R = spec.rank
+    for mode in (0, 2, 4):
+        total = torch.zeros((spec.dims[mode], R), device="cuda")
+        for i in range(parts):
+            out = torch.empty((spec.dims[mode], R), device="cuda")
+            blco.blco_mttkrp_range(t.handle, mode, int(b[i]), int(b[i + 1]), A, blco.BLCO_F32, R, out)
+            M, S = oracle.mttkrp(cs[b[i]:b[i + 1]], vs[b[i]:b[i + 1]], spec.dims, Af, mode)
+            assert oracle.max_rel_err(out.cpu().numpy(), M, S) <= FP32_TOL, (mode, i)
+            total += out
+        M, S = oracle.mttkrp(cs, vs, spec.dims, Af, mode)
+        assert oracle.max_rel_err(total.cpu().numpy(), M, S) <= 2 * FP32_TOL
+    # empty range: zeros; unaligned begin and a streamed store are refused
+    out = torch.full((spec.dims[0], R), 7.0, device="cuda")
+    blco.blco_mttkrp_range(t.handle, 0, 64, 64, A, blco.BLCO_F32, R, out)
+    assert torch.all(out == 0)
+    with pytest.raises(blco.BlcoError) as ei:
+        blco.blco_mttkrp_range(t.handle, 0, 33, 64, A, blco.BLCO_F32, R, out)
+    assert ei.value.status == blco.BLCO_ERR_ARG
+    ts = blco.Tensor.build(coords, vals, spec.dims, force_stream=True)
+    with pytest.raises(blco.BlcoError) as ei:
+        blco.blco_mttkrp_range(ts.handle, 0, 0, 64, A, blco.BLCO_F32, R, out)
+    assert ei.value.status == blco.BLCO_ERR_STATE
+
+
 def test_argument_errors():
     spec = synth.small(0, 1000, (10, 20, 30))
     coords, vals, A = make(spec)
@@ -372,6 +475,29 @@ def test_cp_bwd_is_mttkrp_with_gradient_values():
         assert oracle.max_rel_err(out, M, S) <= FP32_TOL
 
 
+@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])
+@pytest.mark.parametrize("R", [16, 64])
+def test_cp_bwd_16bit_factors(dtype, R):
+    """The adjoint with 16-bit factors (float32 accumulation): against the
+    FP64 oracle on the rounded factors (accumulation error only) and on the
+    unrounded float32 factors (the factor rounding, bound 1e-2)."""
+    spec = synth.small(4, 150_000, (1 << 14, 1 << 14, 1 << 10))
+    coords, vals, _ = make(spec)
+    A = synth.factors(spec, rank=R, device="cuda", dist="normal")
+    A16 = [blco.convert(a, dtype) for a in A]
+    t = blco.Tensor.build(coords, vals, spec.dims)
+    g = torch.randn(spec.nnz, device="cuda")
+    c = coords.cpu().numpy()[t.perm()]
+    gn = g.cpu().numpy().astype(np.float64)
+    Ar = rounded16(A, dtype)
+    for n in range(3):
+        out = t.cp_bwd(n, g, A16).cpu().numpy()
+        M, S = oracle.mttkrp(c, gn, spec.dims, Ar, n)
+        assert oracle.max_rel_err(out, M, S) <= FP32_TOL
+        M, S = oracle.mttkrp(c, gn, spec.dims, to_np64(A), n)
+        assert oracle.max_rel_err(out, M, S) <= BF16_TOL
+
+
 def test_sparse_cp_autograd():
     spec = synth.small(4, 50_000, (1 << 12, 1 << 12, 1 << 8))
     coords, vals, _ = make(spec)
@@ -406,9 +532,9 @@ def test_gram_and_update_match_oracle():
     info = torch.zeros(1, dtype=torch.int32, device="cuda")
     blco.blco_cpals_update(G, 3, 0, R, M, 300, out, lam, Gn, info)
     V = oracle.gram(A[1].cpu().numpy().astype(np.float64)) * oracle.gram(A[2].cpu().numpy().astype(np.float64))
-    ref = oracle.cpals.solve_right(M.cpu().numpy().astype(np.float64), V)
+    ref, rinfo = oracle.cpals.solve_right(M.cpu().numpy().astype(np.float64), V)
     lref = np.linalg.norm(ref, axis=0)
-    assert int(info.item()) == 0
+    assert int(info.item()) == rinfo == 0
     np.testing.assert_allclose(lam.cpu().numpy(), lref, rtol=1e-5)
     np.testing.assert_allclose(out.cpu().numpy(), ref / lref, rtol=1e-4, atol=1e-6)
 
@@ -432,27 +558,44 @@ def test_gram_float32_pairs_match_fp64(R):
     assert np.max(np.abs(Gh - Gh.T) / scale) <= 1e-13  # symmetric up to the order of the CTA sums
 
 
-def test_update_pseudo_inverse_path():
-    R = 8
-    # rank-deficient Grams: identical columns make V singular
-    a = np.random.default_rng(4).standard_normal((50, R)).astype(np.float32)
-    a[:, 1] = a[:, 0]
-    A = torch.from_numpy(a).cuda()
-    G = torch.empty((R, R), dtype=torch.float64, device="cuda")
-    blco.blco_gram(A, blco.BLCO_F32, 50, R, G)
-    M = torch.from_numpy(np.random.default_rng(5).standard_normal((40, R)).astype(np.float32)).cuda()
+@pytest.mark.parametrize("R,N", [(8, 2), (16, 3), (64, 3)])
+def test_update_pseudo_inverse_path(R, N):
+    """Two equal columns in every other factor make V singular: the update
+    must take the pseudo-inverse branch (info 1) and give the oracle's
+    A = M V^+ (normalised columns) and lambda, from the same Grams."""
+    rng = np.random.default_rng(4 + R)
+    dims = [50 + 10 * k for k in range(N)]
+    G = []
+    for d in dims:
+        a = rng.standard_normal((d, R)).astype(np.float32)
+        a[:, 1] = a[:, 0]
+        g = torch.empty((R, R), dtype=torch.float64, device="cuda")
+        blco.blco_gram(torch.from_numpy(a).cuda(), blco.BLCO_F32, d, R, g)
+        G.append(g)
+    mode = N - 1
+    I = 40
+    M = torch.from_numpy(rng.standard_normal((I, R)).astype(np.float32)).cuda()
     out = torch.empty_like(M)
     lam = torch.empty(R, dtype=torch.float64, device="cuda")
     info = torch.zeros(1, dtype=torch.int32, device="cuda")
-    blco.blco_cpals_update([G, G], 2, 1, R, M, 40, out, lam, None, info)
+    blco.blco_cpals_update(G, N, mode, R, M, I, out, lam, None, info)
     assert int(info.item()) == 1
-    V = G.cpu().numpy()
-    ref = M.cpu().numpy().astype(np.float64) @ np.linalg.pinv(V, rcond=1e-10, hermitian=True)
+    V = np.ones((R, R))
+    for k in range(N):
+        if k != mode:
+            V = V * G[k].cpu().numpy()
+    ref, rinfo = oracle.cpals.solve_right(M.cpu().numpy().astype(np.float64), V)
+    assert rinfo == 1
     lref = np.linalg.norm(ref, axis=0)
+    # V^+ is applied in float32 on the GPU: relative error ~ cond(V restricted to its range) * 2^-24
     np.testing.assert_allclose(lam.cpu().numpy(), lref, rtol=1e-4)
+    np.testing.assert_allclose(out.cpu().numpy(), ref / lref, rtol=0, atol=1e-4)
 
 
 def test_cp_als_tracks_oracle_and_recovers_planted():
+    """GPU CP-ALS (float32 MTTKRP, FP64 R x R algebra) against the FP64 oracle
+    CP-ALS from the same initial factors: every factor (columns up to sign)
+    and lambda after 1, 5 and 20 sweeps, and recovery of the planted model."""
     rng = np.random.default_rng(15)
     dims = (30, 25, 20)
     R = 8
@@ -462,10 +605,19 @@ def test_cp_als_tracks_oracle_and_recovers_planted():
     v = np.einsum("ir,jr,kr->ijk", *P)[tuple(c.T)]
     t = blco.Tensor.build(torch.from_numpy(c.astype(np.int32)).cuda(), torch.from_numpy(v.astype(np.float32)).cuda(),
                           dims)
-    init = [rng.standard_normal((d, R)) for d in dims]
-    A = [torch.from_numpy(a.astype(np.float32)).cuda() for a in init]
-    _, lam, fits = blco.cp_als(t, A, iters=60)
-    _, _, rfits = oracle.cp_als(c, v.astype(np.float32).astype(np.float64), dims,
-                                [a.astype(np.float32).astype(np.float64) for a in init], iters=60)
+    init = [rng.standard_normal((d, R)).astype(np.float32) for d in dims]
+    v32 = v.astype(np.float32).astype(np.float64)
+    for iters in (1, 5, 20):
+        A = [torch.from_numpy(a.copy()).cuda() for a in init]
+        _, lam, fits = blco.cp_als(t, A, iters=iters)
+        rA, rlam, rfits = oracle.cp_als(c, v32, dims, [a.astype(np.float64) for a in init], iters=iters)
+        lam = lam.cpu().numpy()
+        np.testing.assert_allclose(lam, rlam, rtol=1e-4)
+        for n in range(3):
+            got = A[n].cpu().numpy().astype(np.float64)
+            sign = np.sign(np.sum(got * rA[n], axis=0))
+            assert np.all(sign != 0)
+            np.testing.assert_allclose(got * sign, rA[n], rtol=0, atol=1e-4)
+        assert abs(fits[-1] - rfits[-1]) < 1e-5
+    _, _, fits = blco.cp_als(t, [torch.from_numpy(a.copy()).cuda() for a in init], iters=60)
     assert fits[-1] > 0.999
-    assert abs(fits[4] - rfits[4]) < 1e-3
