@@ -184,6 +184,29 @@ blco_status blco_mttkrp_range(blco_handle h, int mode, int64_t begin, int64_t en
                               blco_dtype fdt, int R, float *out, blco_stream stream);
 
 /*
+ * float64 values, factors and accumulation -- the precision of the paper's
+ * evaluation (Section 6: double-precision values). blco_build_f64 builds the
+ * same store as blco_build (same keys, order, blocks) holding the values as
+ * float64 (vals: nnz doubles, host or device); it keeps the store on the
+ * device (BLCO_ERR_UNSUPPORTED when force_stream is set or the device budget
+ * would stream it). blco_mttkrp_f64 is Eq. 1 on such a store:
+ *   factors  N pointers (host or device) to I_k x R float64 matrices,
+ *            factors[mode] not read
+ *   R        8, 16, 32 or 64 (BLCO_ERR_UNSUPPORTED otherwise)
+ *   out      I_mode x R float64 (host or device), overwritten
+ * accumulated in float64 (run sums, per-warp shared-memory copies of the hot
+ * rows, red.global.add.f64), so only the summation order differs from the
+ * exact-rounding FP64 definition. A float64 store serves blco_mttkrp_f64,
+ * blco_perm, blco_keys, blco_blocks, blco_info and blco_destroy; the float32
+ * calls (blco_mttkrp*, blco_cp_*, blco_values, blco_norm2) return
+ * BLCO_ERR_STATE on it, and blco_mttkrp_f64 on a float32 store too.
+ */
+blco_status blco_build_f64(const uint32_t *coords, const double *vals, int64_t nnz, const int64_t *dims, int N,
+                           const blco_build_opts *opts, blco_stream stream, blco_handle *out);
+blco_status blco_mttkrp_f64(blco_handle h, int mode, const double *const *factors, int R, double *out,
+                            blco_stream stream);
+
+/*
  * CP model at every stored nonzero (Algorithm 1's model, Section 2.2):
  *   xhat[j] = sum_r prod_n A_n[i_n^j, r], j in store order.
  *   factors  N matrices I_n x R (host or device); xhat: nnz float32 (host or device)

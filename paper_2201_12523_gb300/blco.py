@@ -35,7 +35,7 @@ EXPORTS = ["blco_default_opts", "blco_build", "blco_mttkrp", "blco_mttkrp_all", 
            "blco_values", "blco_perm", "blco_keys", "blco_blocks", "blco_info", "blco_sync", "blco_destroy",
            "blco_last_error", "blco_convert", "blco_gram", "blco_cpals_update", "blco_cpals_fit", "blco_norm2",
            "blco_profile_enable", "blco_profile_read", "blco_cpals_update_noalloc", "blco_inject_fault",
-           "blco_partition", "blco_mttkrp_range"]
+           "blco_partition", "blco_mttkrp_range", "blco_build_f64", "blco_mttkrp_f64"]
 
 
 class BuildOpts(ctypes.Structure):
@@ -78,6 +78,8 @@ def _load():
         "blco_mttkrp": [vp, i32, vp, i32, i32, vp, vp],
         "blco_mttkrp_all": [vp, vp, i32, i32, vp, vp],
         "blco_partition": [i64, i32, vp],
+        "blco_build_f64": [vp, vp, i64, vp, i32, vp, vp, vp],
+        "blco_mttkrp_f64": [vp, i32, vp, i32, vp, vp],
         "blco_mttkrp_range": [vp, i32, i64, i64, vp, i32, i32, vp, vp],
         "blco_cp_fwd": [vp, vp, i32, i32, vp, vp],
         "blco_cp_bwd": [vp, i32, vp, vp, i32, i32, vp, vp],
@@ -192,6 +194,22 @@ def blco_build(coords, vals, dims: Sequence[int], opts: Optional[BuildOpts] = No
                          _stream(stream), ctypes.byref(h))
     _check("blco_build", st)
     return h
+
+
+def blco_build_f64(coords, vals, dims: Sequence[int], opts: Optional[BuildOpts] = None, stream=None) -> ctypes.c_void_p:
+    nnz = int(coords.shape[0])
+    N = len(dims)
+    d = (ctypes.c_int64 * N)(*[int(x) for x in dims])
+    h = ctypes.c_void_p()
+    st = _lib.blco_build_f64(_ptr(coords), _ptr(vals), nnz, d, N, ctypes.byref(opts) if opts is not None else None,
+                             _stream(stream), ctypes.byref(h))
+    _check("blco_build_f64", st)
+    return h
+
+
+def blco_mttkrp_f64(h, mode: int, factors: Sequence, R: int, out, stream=None):
+    _check("blco_mttkrp_f64", _lib.blco_mttkrp_f64(h, int(mode), _ptr_array(factors), int(R), _ptr(out),
+                                                   _stream(stream)))
 
 
 def blco_mttkrp(h, mode: int, factors: Sequence, fdt: int, R: int, out, stream=None):
@@ -330,6 +348,8 @@ class Tensor:
         o.device_budget_bytes = int(device_budget_bytes)
         o.force_stream = 1 if force_stream else 0
         o.compensated_sums = 1 if compensated_sums else 0
+        if getattr(vals, "dtype", None) in (torch.float64, np.float64):
+            return cls(blco_build_f64(coords, vals, dims, o, stream), dims)
         return cls(blco_build(coords, vals, dims, o, stream), dims)
 
     @property
@@ -355,6 +375,14 @@ class Tensor:
             dev = next(f.device for f in factors if f is not None)
             out = torch.empty((self.dims[mode], R), dtype=torch.float32, device=dev)
         blco_mttkrp(self.handle, mode, factors, _fdt(factors), R, out, stream)
+        return out
+
+    def mttkrp_f64(self, mode: int, factors: Sequence, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        """Mode-`mode` MTTKRP of a store built with float64 values, float64 factors (Section 6's precision)."""
+        R = int(factors[(mode + 1) % len(factors)].shape[1])
+        if out is None:
+            out = torch.empty((self.dims[mode], R), dtype=torch.float64, device=factors[(mode + 1) % len(factors)].device)
+        blco_mttkrp_f64(self.handle, mode, factors, R, out, stream)
         return out
 
     def mttkrp_all(self, factors: Sequence, outs: Optional[List[torch.Tensor]] = None, stream=None):

@@ -91,6 +91,8 @@ struct blco_tensor {
     // store (device when resident, pinned host when streamed)
     uint64_t *d_keys = nullptr;
     float *d_vals = nullptr;
+    double *d_vals64 = nullptr;  // float64 values (stores built by blco_build_f64)
+    bool f64 = false;
     uint32_t *d_perm = nullptr;
     uint64_t *h_keys = nullptr;
     float *h_vals = nullptr;
@@ -172,6 +174,7 @@ struct blco_tensor {
         sv.key_origin = 0;
         sv.vals = d_vals;
         sv.val_origin = 0;
+        sv.vals64 = d_vals64;
         sv.begin = 0;
         sv.end = nnz;
         sv.tile_block = d_tile_block;
@@ -196,6 +199,7 @@ void release(blco_tensor *h) {
     cudaDeviceSynchronize();
     h->dfree(h->d_keys, 0);
     h->dfree(h->d_vals, 0);
+    h->dfree(h->d_vals64, 0);
     h->dfree(h->d_perm, 0);
     h->dfree(h->d_bstart, 0);
     h->dfree(h->d_bbase, 0);
@@ -479,6 +483,7 @@ blco_status mttkrp_device(blco_tensor *h, int mode, const FactorSet &fs, blco_dt
 
 blco_status check_common(blco_tensor *h, blco_dtype fdt, int R) {
     if (!h) return fail(BLCO_ERR_ARG, "handle is NULL");
+    if (h->f64) return fail(BLCO_ERR_STATE, "the store holds float64 values; use blco_mttkrp_f64");
     if (!dtype_ok(fdt)) return fail(BLCO_ERR_ARG, "unknown factor dtype");
     if (!rank_supported(R)) return fail(BLCO_ERR_UNSUPPORTED, "rank must be 8, 16, 32, 64 or 128");
     return BLCO_OK;
@@ -506,15 +511,16 @@ blco_status blco_default_opts(blco_build_opts *o) {
     return BLCO_OK;
 }
 
-blco_status blco_build(const uint32_t *coords, const float *vals, int64_t nnz, const int64_t *dims, int N,
-                       const blco_build_opts *opts, blco_stream stream, blco_handle *out) {
+// blco_build, and blco_build_f64's store without float32 values (vals NULL)
+static blco_status build_impl(const uint32_t *coords, const float *vals, int64_t nnz, const int64_t *dims, int N,
+                              const blco_build_opts *opts, blco_stream stream, blco_handle *out, bool no_vals) {
     g_err.clear();
     if (!out) return fail(BLCO_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (N < 1 || N > MAXN) return fail(BLCO_ERR_ARG, "order N must be in 1..8");
     if (!dims) return fail(BLCO_ERR_ARG, "dims is NULL");
     if (nnz < 0 || nnz >= ((int64_t)1 << 32) - 64) return fail(BLCO_ERR_ARG, "nnz must be in 0..2^32-65");
-    if (nnz > 0 && (!coords || !vals)) return fail(BLCO_ERR_ARG, "coords/vals is NULL");
+    if (nnz > 0 && (!coords || (!vals && !no_vals))) return fail(BLCO_ERR_ARG, "coords/vals is NULL");
     blco_build_opts o;
     blco_default_opts(&o);
     if (opts) {
@@ -568,7 +574,7 @@ blco_status blco_build(const uint32_t *coords, const float *vals, int64_t nnz, c
         if (e != cudaSuccess) BAIL(cuda_fail(e, "coordinate upload"));
         dc = tc;
     }
-    if (nnz > 0 && !is_device_ptr(vals)) {
+    if (nnz > 0 && vals && !is_device_ptr(vals)) {
         e = cudaMallocAsync(&tv, sizeof(float) * nnz, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(tv, vals, sizeof(float) * nnz, cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) BAIL(cuda_fail(e, "value upload"));
@@ -702,6 +708,135 @@ cleanup:
     }
     cudaStreamSynchronize(s);
     *out = h;
+    return BLCO_OK;
+}
+
+blco_status blco_build(const uint32_t *coords, const float *vals, int64_t nnz, const int64_t *dims, int N,
+                       const blco_build_opts *opts, blco_stream stream, blco_handle *out) {
+    return build_impl(coords, vals, nnz, dims, N, opts, stream, out, false);
+}
+
+blco_status blco_build_f64(const uint32_t *coords, const double *vals, int64_t nnz, const int64_t *dims, int N,
+                           const blco_build_opts *opts, blco_stream stream, blco_handle *out) {
+    g_err.clear();
+    if (!out) return fail(BLCO_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (nnz > 0 && !vals) return fail(BLCO_ERR_ARG, "vals is NULL");
+    if (opts && opts->force_stream) return fail(BLCO_ERR_UNSUPPORTED, "float64 stores are kept on the device");
+    blco_handle h = nullptr;
+    blco_status st = build_impl(coords, nullptr, nnz, dims, N, opts, stream, &h, true);
+    if (st != BLCO_OK) return st;
+    if (h->streamed) {
+        release(h);
+        return fail(BLCO_ERR_UNSUPPORTED, "float64 stores are kept on the device (the budget would stream it)");
+    }
+    DeviceGuard g(h->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const double *dv = vals;
+    double *tv = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (nnz > 0 && !is_device_ptr(vals)) {
+        e = cudaMallocAsync(&tv, sizeof(double) * nnz, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(tv, vals, sizeof(double) * nnz, cudaMemcpyHostToDevice, s);
+        dv = tv;
+    }
+    if (e == cudaSuccess) e = h->dalloc((void **)&h->d_vals64, sizeof(double) * h->npad);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_vals64, 0, sizeof(double) * h->npad, s);
+    if (e == cudaSuccess) e = gather_f64(dv, h->d_perm, nnz, h->d_vals64, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (tv) cudaFreeAsync(tv, s);
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(s);
+        release(h);
+        return cuda_fail(e, "float64 values");
+    }
+    h->dfree(h->d_vals, 0);  // the float32 values (zeros) are not kept
+    h->dev_bytes -= (int64_t)sizeof(float) * h->npad;
+    h->d_vals = nullptr;
+    h->f64 = true;
+    if (h->budget > 0 && h->dev_bytes > h->budget) {
+        release(h);
+        return fail(BLCO_ERR_OOM, "device budget exceeded");
+    }
+    *out = h;
+    return BLCO_OK;
+}
+
+blco_status blco_mttkrp_f64(blco_handle h, int mode, const double *const *factors, int R, double *out,
+                            blco_stream stream) {
+    g_err.clear();
+    if (!h) return fail(BLCO_ERR_ARG, "handle is NULL");
+    if (!h->f64) return fail(BLCO_ERR_STATE, "the store holds float32 values; use blco_mttkrp");
+    if (!rank_supported_f64(R)) return fail(BLCO_ERR_UNSUPPORTED, "rank must be 8, 16, 32 or 64");
+    if (mode < 0 || mode >= h->L.N) return fail(BLCO_ERR_ARG, "mode out of range");
+    if (!out) return fail(BLCO_ERR_ARG, "out is NULL");
+    if (reinterpret_cast<uintptr_t>(out) & 15) return fail(BLCO_ERR_ARG, "out is not 16-byte aligned");
+    std::string why;
+    if (!check_factors(h, reinterpret_cast<const void *const *>(factors), mode, why)) return fail(BLCO_ERR_ARG, why);
+    DeviceGuard g(h->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // host arguments are staged in the workspace
+    const int N = h->L.N;
+    bool host_in[MAXN] = {};
+    size_t off[MAXN] = {}, total = 0;
+    for (int k = 0; k < N; ++k) {
+        if (k == mode) continue;
+        host_in[k] = !is_device_ptr(factors[k]);
+        if (host_in[k]) {
+            off[k] = total;
+            total += ((size_t)h->L.dims[k] * R * sizeof(double) + 255) / 256 * 256;
+        }
+    }
+    const bool host_out = !is_device_ptr(out);
+    const size_t out_bytes = (size_t)h->L.dims[mode] * R * sizeof(double);
+    const size_t out_off = total;
+    if (host_out) total += (out_bytes + 255) / 256 * 256;
+    char *base = nullptr;
+    if (total > 0) {
+        void *p = nullptr;
+        cudaError_t e = h->workspace(total, &p);
+        if (e != cudaSuccess) return cuda_fail(e, "staging workspace");
+        base = static_cast<char *>(p);
+    }
+    const double *fs[MAXN] = {};
+    for (int k = 0; k < N; ++k) {
+        if (k == mode) continue;
+        fs[k] = factors[k];
+        if (host_in[k]) {
+            cudaError_t e = cudaMemcpyAsync(base + off[k], factors[k], (size_t)h->L.dims[k] * R * sizeof(double),
+                                            cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) return cuda_fail(e, "factor upload");
+            fs[k] = reinterpret_cast<const double *>(base + off[k]);
+        }
+    }
+    double *o = host_out ? reinterpret_cast<double *>(base + out_off) : out;
+    HotRows hot;
+    hot.rows = h->d_hot[mode];
+    hot.count = h->hot_count[mode];
+    hot.dense = 0;
+    if (h->L.dims[mode] <= warp_tier_capacity_f64(R)) {
+        hot.rows = nullptr;
+        hot.count = (int)h->L.dims[mode];
+        hot.dense = 1;
+    }
+    const int64_t n = h->L.dims[mode] * (int64_t)R;
+    cudaError_t e = timed(h, "zero", s, [&]() { return launch_zero(reinterpret_cast<float *>(o), 2 * n, s); });
+    if (e != cudaSuccess) return cuda_fail(e, "zero output");
+    if (h->nnz > 0) {
+        StoreView sv = h->view();
+        e = timed(h, "mttkrp_f64", s, [&]() { return launch_mttkrp_f64(sv, fs, R, mode, hot, o, s); });
+        if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    }
+    if (host_out) {
+        e = cudaMemcpyAsync(out, o, out_bytes, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return cuda_fail(e, "result download");
+    }
+    if (total > 0) {
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "mttkrp_f64");
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "mttkrp_f64");
     return BLCO_OK;
 }
 
@@ -1058,6 +1193,7 @@ static blco_status copy_out(blco_tensor *h, void *dst, const void *dsrc, const v
 blco_status blco_values(blco_handle h, float *vals, blco_stream stream) {
     g_err.clear();
     if (!h || (!vals && h->nnz > 0)) return fail(BLCO_ERR_ARG, "NULL argument");
+    if (h->f64) return fail(BLCO_ERR_STATE, "the store holds float64 values");
     DeviceGuard g(h->device);
     return copy_out(h, vals, h->d_vals, h->h_vals, sizeof(float) * h->nnz, reinterpret_cast<cudaStream_t>(stream));
 }
@@ -1188,6 +1324,7 @@ blco_status blco_cpals_fit(double normX2, const double *const *grams, int N, int
 blco_status blco_norm2(blco_handle h, double *out, blco_stream stream) {
     g_err.clear();
     if (!h || !out) return fail(BLCO_ERR_ARG, "NULL argument");
+    if (h->f64) return fail(BLCO_ERR_STATE, "the store holds float64 values");
     DeviceGuard g(h->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = launch_norm2(nullptr, 0, out, s);  // zeroes *out

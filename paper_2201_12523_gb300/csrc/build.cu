@@ -382,9 +382,15 @@ __global__ void k_reencode(const uint32_t *__restrict__ coords, const float *__r
             }
         }
         skeys[j] = key;
-        svals[j] = vals[p];
+        svals[j] = vals ? vals[p] : 0.f;  // no float32 values: a float64 store gathers its own
         if (a.has_blocks) bkey[j] = bk;
     }
+}
+
+__global__ void k_gather_f64(const double *__restrict__ src, const uint32_t *__restrict__ perm, int64_t nnz,
+                             double *__restrict__ dst) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nnz; j += (int64_t)gridDim.x * blockDim.x)
+        dst[j] = src[perm[j]];
 }
 
 __global__ void k_run_flags(const uint64_t *__restrict__ bkey, int64_t n, uint32_t *__restrict__ flags) {
@@ -605,6 +611,12 @@ done:
     if (d_bad) cudaFreeAsync(d_bad, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     return e;
+}
+
+cudaError_t gather_f64(const double *src, const uint32_t *perm, int64_t nnz, double *dst, cudaStream_t s) {
+    if (nnz <= 0) return cudaSuccess;
+    k_gather_f64<<<grid_for(nnz, 256), 256, 0, s>>>(src, perm, nnz, dst);
+    return cudaGetLastError();
 }
 
 cudaError_t build_tile_block(const int64_t *d_bstart, int64_t nblocks, int64_t nnz, uint32_t *tile_block,

@@ -41,6 +41,7 @@ struct StoreView {
     int64_t key_origin;
     const float *vals;      // values (or an upstream gradient) in store order
     int64_t val_origin;
+    const double *vals64;   // float64 values in store order (stores built with them)
     int64_t begin, end;     // store positions processed by this launch
     const uint32_t *tile_block;  // block that holds store position 32 * t
     const int64_t *bstart;       // nblocks + 1 block offsets
@@ -93,6 +94,11 @@ cudaError_t launch_cp_fwd_bf16(const StoreView &sv, const FactorSet &fs, int R, 
 cudaError_t launch_cp_fwd_f16(const StoreView &sv, const FactorSet &fs, int R, float *xhat, int64_t xorigin,
                               cudaStream_t s);
 bool rank_supported(int R);
+// mttkrp_f64.cu: float64 values, factors and output
+cudaError_t launch_mttkrp_f64(const StoreView &sv, const double *const *factors, int R, int mode, const HotRows &hot,
+                              double *out, cudaStream_t s);
+bool rank_supported_f64(int R);
+int warp_tier_capacity_f64(int R);  // rows per launch accumulated on chip at rank R (float64)
 int warp_tier_capacity(int R);  // rows per launch accumulated on chip (per-warp copies) at rank R
 
 // build.cu
@@ -108,6 +114,8 @@ struct BuildOut {
 // are device pointers. Temporary memory via cudaMallocAsync on s.
 cudaError_t build_store(const Layout &L, const uint32_t *coords, const float *vals, int64_t nnz,
                         int64_t cap, BuildOut &out, cudaStream_t s, std::string &why);
+// dst[j] = src[perm[j]] for j < nnz (float64 values into store order)
+cudaError_t gather_f64(const double *src, const uint32_t *perm, int64_t nnz, double *dst, cudaStream_t s);
 cudaError_t build_tile_block(const int64_t *d_bstart, int64_t nblocks, int64_t nnz,
                              uint32_t *tile_block, cudaStream_t s);
 // Per-mode index histogram of the store's nonzeros (counts: I_n uint32).

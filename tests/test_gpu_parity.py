@@ -427,6 +427,69 @@ def test_partitioned_mttkrp_sums_to_the_full_result(parts):
     assert ei.value.status == blco.BLCO_ERR_STATE
 
 
+@pytest.mark.parametrize("R", [8, 16, 32, 64])
+@pytest.mark.parametrize("which", ["3d", "4d", "5d-blocked"])
+def test_mttkrp_f64_matches_oracle(which, R):
+    """float64 values, factors and accumulation (the paper's precision):
+    every mode against the FP64 oracle to 1e-12 of sum |terms| (only the
+    summation order differs), on a skewed 3-mode, a 4-mode and a blocked
+    5-mode store with ragged tails."""
+    if which == "3d":
+        spec = synth.small(1, 60_003, (1 << 12, 1 << 11, 1 << 8))
+        kw = {}
+    elif which == "4d":
+        spec = synth.small(2, 40_001, (1 << 10, 1 << 9, 1 << 8, 1 << 4))
+        kw = {}
+    else:
+        spec = synth.small(3, 30_017, (1 << 24, 1 << 20, 1 << 16, 1 << 12, 1 << 8))
+        kw = dict(max_nnz_per_block=4000)
+    coords, vals32, _ = make(spec)
+    rng = np.random.default_rng(R)
+    v = rng.standard_normal(spec.nnz)  # float64 values with full mantissas
+    A = [rng.standard_normal((d, R)) for d in spec.dims]
+    t = blco.Tensor.build(coords, torch.from_numpy(v).cuda(), spec.dims, **kw)
+    if which == "5d-blocked":
+        assert t.info()["nblocks"] > 1
+    Ad = [torch.from_numpy(a).cuda() for a in A]
+    c = coords.cpu().numpy()
+    for n in range(spec.order):
+        out = t.mttkrp_f64(n, Ad)
+        M, S = oracle.mttkrp(c, v, spec.dims, A, n)
+        assert oracle.max_rel_err(out.cpu().numpy(), M, S) <= 1e-12, n
+    # host factors and a host result
+    outh = np.empty((spec.dims[0], R))
+    blco.blco_mttkrp_f64(t.handle, 0, [None] + A[1:], R, outh)
+    M, S = oracle.mttkrp(c, v, spec.dims, A, 0)
+    assert oracle.max_rel_err(outh, M, S) <= 1e-12
+
+
+def test_f64_store_state_errors():
+    spec = synth.small(0, 5000, (100, 80, 60))
+    coords, vals32, A32 = make(spec)
+    v = vals32.double()
+    t64 = blco.Tensor.build(coords, v, spec.dims)
+    t32 = blco.Tensor.build(coords, vals32, spec.dims)
+    A64 = [a.double() for a in A32]
+    with pytest.raises(blco.BlcoError) as ei:
+        t64.mttkrp(0, A32)
+    assert ei.value.status == blco.BLCO_ERR_STATE
+    with pytest.raises(blco.BlcoError) as ei:
+        t32.mttkrp_f64(0, A64)
+    assert ei.value.status == blco.BLCO_ERR_STATE
+    with pytest.raises(blco.BlcoError) as ei:
+        t64.values()
+    assert ei.value.status == blco.BLCO_ERR_STATE
+    A128 = [torch.zeros((d, 128), dtype=torch.float64, device="cuda") for d in spec.dims]
+    with pytest.raises(blco.BlcoError) as ei:
+        t64.mttkrp_f64(0, A128)
+    assert ei.value.status == blco.BLCO_ERR_UNSUPPORTED
+    with pytest.raises(blco.BlcoError) as ei:
+        blco.Tensor.build(coords, v, spec.dims, force_stream=True)
+    assert ei.value.status == blco.BLCO_ERR_UNSUPPORTED
+    # the float64 store has the float32 store's order and blocks
+    assert np.array_equal(t64.perm(), t32.perm()) and np.array_equal(t64.keys(), t32.keys())
+
+
 def test_argument_errors():
     spec = synth.small(0, 1000, (10, 20, 30))
     coords, vals, A = make(spec)
