@@ -389,7 +389,7 @@ def run_reference(args, ranks: Ranks):
 
 
 # ----------------------------------------------------------------- GPU arm
-def measure_mttkrp(blco, spec, args, ranks, dev, steps, warmup, *, headline, sampler=None):
+def measure_mttkrp(blco, spec, args, ranks, dev, steps, warmup, *, headline, sampler=None, with_f64=False):
     """All-mode MTTKRP of an in-memory or streamed workload. Returns a dict
     (and the headline keys when `headline`)."""
     R = spec.rank
@@ -410,6 +410,10 @@ def measure_mttkrp(blco, spec, args, ranks, dev, steps, warmup, *, headline, sam
     touched = [int(torch.unique(coords[:, n]).numel()) for n in range(spec.order)]
     want_bf16 = not args.no_bf16 and not info["streamed"]
     t_comp = blco.Tensor.build(coords, vals, spec.dims, compensated_sums=True) if (want_bf16 and headline) else None
+    t64 = blco.Tensor.build(coords, vals.double(), spec.dims) if with_f64 else None
+    # a streamed workload is also timed on a store resident on the device: the
+    # same all-mode MTTKRP without the host link
+    t_res = blco.Tensor.build(coords, vals, spec.dims) if info["streamed"] else None
     need_host = headline and (not args.no_errors or not args.no_cpu) and ranks.rank == 0
     c_h = coords.cpu().numpy().view(np.uint32) if need_host else None
     v_h = vals.cpu().numpy() if need_host else None
@@ -476,6 +480,20 @@ def measure_mttkrp(blco, spec, args, ranks, dev, steps, warmup, *, headline, sam
                             "peak_source": "pinned cudaMemcpyAsync H2D, 2 GiB x 5, same run"}
         res["store"]["queues"] = f"{info['n_queues']} queues x {info['queue_nnz']} nonzeros, device budget " \
                                  f"{budget >> 30} GiB"
+        outs_r = [torch.empty_like(o) for o in outs]
+        step_r = make_step(A, t_res, outs_r)
+        for _ in range(warmup):
+            step_r()
+        ms_r = ranks.max(time_steps(step_r, steps, stream)) / steps
+        t_res.destroy()
+        t_res = None
+        del outs_r
+        link_ms = moved / (link * 1e9) * 1e3
+        res["host_link"]["resident_ms_per_step"] = ms_r
+        res["host_link"]["link_ms_per_step_at_peak"] = link_ms
+        res["host_link"]["bound"] = ("kernels: the all-mode MTTKRP of a resident store takes %.0f ms, longer than "
+                                     "the %.0f ms the host link needs for the store at its measured peak" % (ms_r, link_ms)
+                                     if ms_r > link_ms else "host link")
 
     # bfloat16 factors, same step; Kahan-compensated run sums on the second store
     err_results = {}
@@ -511,6 +529,29 @@ def measure_mttkrp(blco, spec, args, ranks, dev, steps, warmup, *, headline, sam
             t_comp = None
         del A16
     err_results["f32"] = (outs, "f32")
+
+    # float64 values, factors and accumulation (the paper's precision), same step
+    if t64 is not None:
+        A64 = [a.double() for a in A]
+        outs64 = [torch.empty((d, R), dtype=torch.float64, device=dev) for d in spec.dims]
+
+        def step64():
+            for n in range(spec.order):
+                t64.mttkrp_f64(n, A64, out=outs64[n])
+        for _ in range(warmup):
+            step64()
+        blco.blco_profile_enable(t64.handle, True)
+        ms64 = ranks.max(time_steps(step64, steps, stream))
+        blco.blco_profile_enable(t64.handle, False)
+        p64 = blco.blco_profile_read(t64.handle)
+        b64 = sum(16 * spec.nnz + 8 * R * sum(spec.dims) for _ in range(spec.order)) / spec.order
+        ach64, kms64, _ = kernel_roofline(p64, "mttkrp_f64", b64, peak)
+        res["f64"] = {"value": ranks.rate(spec.nnz * steps, ms64 / 1e3), "ms_per_step": ms64 / steps,
+                      "ms_per_launch": kms64, "roofline_frac": (ach64 / peak) if ach64 else None,
+                      "algorithmic_bytes_per_launch": b64, "speedup_vs_f32": ms_max / ms64,
+                      "note": "float64 values, factors, accumulation and output (blco_mttkrp_f64)"}
+        t64.destroy()
+        del A64, outs64
 
     # end to end through the C ABI with host buffers
     if headline and not args.no_e2e:
@@ -668,7 +709,7 @@ def run_blco(args, ranks: Ranks):
             else:
                 streamed = extra in STREAMED
                 r = measure_mttkrp(blco, es, args, ranks, dev, 3 if streamed else 10, 2 if streamed else 3,
-                                   headline=False)
+                                   headline=False, with_f64=not streamed)
             r["wall_s"] = time.perf_counter() - t0
             line["workloads"][extra] = r
     if ranks.rank == 0:
