@@ -63,8 +63,8 @@ FP32_TOL, BF16_TOL = 1e-5, 1e-2
 # (profiles/), valid only for the kernel source it was taken from (sha256 of
 # the kernel header and its float32 translation unit): workload -> record.
 TRAFFIC_RECORDS = {
-    "zipf1.1-4d-500M": {"src_sha256": "e857c8a5075914663cabe1454676e5a41d0cae9867f4c1802d6a81f4c1b1bede",
-                        "bytes_per_launch": 6.735e9},  # mean of modes 0-3, R = 32, float32 factors
+    "zipf1.1-4d-500M": {"src_sha256": "84f2d702736a96d53f1cfa0ff02524c674ad35023ac4a7f99839c1dcba10d5e1",
+                        "bytes_per_launch": 7.204e9},  # mean of modes 0-3, R = 32, float32 factors
 }
 
 

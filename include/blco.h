@@ -153,7 +153,10 @@ blco_status blco_mttkrp(blco_handle h, int mode, const void *const *factors, blc
  * in the order the modes need them; each mode's kernel waits only for the
  * factors it gathers, and each host result is downloaded on a second copy
  * stream while the next mode runs. The call returns when the host results
- * are complete.
+ * are complete. On a streamed store each batch of blocks crosses the host
+ * link once per call: while it sits in its queue's reservation the kernels
+ * of every requested mode run on it (Section 4.2); the factors and all the
+ * requested outputs stay on the device meanwhile.
  */
 blco_status blco_mttkrp_all(blco_handle h, const void *const *factors, blco_dtype fdt, int R,
                             float *const *outs, blco_stream stream);

@@ -302,15 +302,17 @@ struct Stage {
 // -------------------------------------------------------------------------
 // MTTKRP
 // -------------------------------------------------------------------------
-// Resident CTAs per SM the register budget is sized for (80 registers for
-// 3, 128 for 2). Measured on GB300: the MTTKRP kernel is fastest with 3 up
-// to R = 32 (also with 3 gathered modes: -10% at 4 modes) and at R = 64 with
-// two gathered modes (82 registers, hence 2 CTAs, made the planted 3-mode
-// R = 64 adjoint 15% slower); more gathered rows at R = 64 keep 2. The
-// CP-model kernel keeps 2 where it gathers 3 or more rows.
+// Resident CTAs per SM the register budget is sized for (64 registers for
+// 4, 80 for 3, 128 for 2). Measured on GB300: the MTTKRP kernel is fastest
+// with 4 up to R = 32, loading the rows of 2 positions at a time (3 CTAs
+// with 4 positions: 3% slower on the 3-mode Zipf workload, 4% on the 4-mode
+// one); with 3 at R = 64 and two gathered modes (82 registers, hence 2
+// CTAs, made the planted 3-mode R = 64 adjoint 15% slower); more gathered
+// rows at R = 64 keep 2. The CP-model kernel keeps 2 where it gathers 3 or
+// more rows.
 template <int R, int NG>
 __host__ __device__ constexpr int mttkrp_min_ctas() {
-    return (NG == 0 || R > 64 || (R == 64 && NG > 2)) ? 2 : 3;
+    return (NG == 0 || R > 64 || (R == 64 && NG > 2)) ? 2 : (R <= 32 ? 4 : 3);
 }
 template <int R, int NG>
 __host__ __device__ constexpr int cp_min_ctas() {
@@ -324,7 +326,10 @@ __global__ void __launch_bounds__(kThreads, mttkrp_min_ctas<R, NG>()) k_mttkrp(c
     constexpr int G = R / VEC;   // lanes per nonzero
     static_assert(G >= 1 && G <= 32 && (32 % G) == 0, "rank must give 1..32 lanes per row");
     constexpr int STEPS = G;     // sorted positions per subgroup (P = 32 / G subgroups)
-    constexpr int CH = STEPS < 16 / VEC ? STEPS : 16 / VEC;  // positions per register batch (16 floats)
+    // positions whose row loads are issued back to back: 8 elements of each
+    // gathered row per lane at 4 CTAs per SM, 16 otherwise
+    constexpr int CHE = mttkrp_min_ctas<R, NG>() == 4 ? 8 : 16;
+    constexpr int CH = STEPS < CHE / VEC ? STEPS : CHE / VEC;
     constexpr int NS = gather_slots<NG>();
 
     extern __shared__ __align__(16) unsigned char smem[];
