@@ -308,15 +308,18 @@ struct Stage {
 // with 4 positions: 3% slower on the 3-mode Zipf workload, 4% on the 4-mode
 // one); with 3 at R = 64 and two gathered modes (82 registers, hence 2
 // CTAs, made the planted 3-mode R = 64 adjoint 15% slower); more gathered
-// rows at R = 64 keep 2. The CP-model kernel keeps 2 where it gathers 3 or
-// more rows.
+// rows at R = 64 keep 2. The CP-model kernel runs 3 (80 registers) with
+// batches of 16 elements per gathered row and one reduce-scatter per G
+// positions: 8% faster at R = 64 (the planted 3-mode workload) and 14% at
+// R = 32 (the 3-mode Zipf shape) than 2 CTAs with 32-element batches and a
+// shuffle reduction per position.
 template <int R, int NG>
 __host__ __device__ constexpr int mttkrp_min_ctas() {
     return (NG == 0 || R > 64 || (R == 64 && NG > 2)) ? 2 : (R <= 32 ? 4 : 3);
 }
 template <int R, int NG>
 __host__ __device__ constexpr int cp_min_ctas() {
-    return (R >= 64 || NG == 0 || NG >= 3) ? 2 : 3;
+    return NG == 0 ? 2 : 3;
 }
 
 template <typename T, int R, int NG, bool COMP>
@@ -584,7 +587,7 @@ __global__ void __launch_bounds__(kThreads, cp_min_ctas<R, NG>()) k_cp_fwd(const
     constexpr int H = VEC / 2;
     constexpr int G = R / VEC;
     constexpr int STEPS = G;
-    constexpr int CH = STEPS < 32 / VEC ? STEPS : 32 / VEC;  // positions per register batch (32 floats)
+    constexpr int CH = STEPS < 16 / VEC ? STEPS : 16 / VEC;  // positions per register batch (16 floats)
     constexpr int NS = gather_slots<NG>();
     __shared__ Stage<NG> stage[kWarps];
     const int lane = threadIdx.x & 31;
@@ -613,6 +616,7 @@ __global__ void __launch_bounds__(kThreads, cp_min_ctas<R, NG>()) k_cp_fwd(const
         for (int q = 0; q < NS; ++q)
             if (q < ng) st.idx[q][lane] = valid ? o[q] : 0u;
         __syncwarp();
+        float parts[STEPS];  // partial sum over this lane's elements, per position
 #pragma unroll
         for (int c0 = 0; c0 < STEPS; c0 += CH) {
             f2 pr[CH][H];
@@ -642,11 +646,25 @@ __global__ void __launch_bounds__(kThreads, cp_min_ctas<R, NG>()) k_cp_fwd(const
                     unpack2(pr[j][h], a, b);
                     part += a + b;
                 }
-#pragma unroll
-                for (int off = G / 2; off >= 1; off >>= 1) part += __shfl_xor_sync(kFull, part, off);
-                if (c == 0) st.val[g * STEPS + c0 + j] = part;
+                parts[c0 + j] = part;
             }
         }
+        // reduce-scatter of the G positions' partial sums over the subgroup's
+        // G lanes (G - 1 shuffles instead of log2(G) per position): in the
+        // round with distance hh a lane keeps the half of its sums whose
+        // position has bit hh equal to its own lane bit and sends the other
+        // half to lane ^ hh, so lane c ends with the sum of position g*G + c
+#pragma unroll
+        for (int hh = G / 2; hh >= 1; hh >>= 1) {
+            const bool up = (c & hh) != 0;
+#pragma unroll
+            for (int i = 0; i < hh; ++i) {
+                const float send = up ? parts[i] : parts[i + hh];
+                const float keep = up ? parts[i + hh] : parts[i];
+                parts[i] = keep + __shfl_xor_sync(kFull, send, hh);
+            }
+        }
+        st.val[g * STEPS + c] = parts[0];
         __syncwarp();
         if (valid) p.out[pos - p.out_origin] = st.val[lane];
         __syncwarp();
