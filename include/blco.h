@@ -140,6 +140,7 @@ blco_status blco_build(const uint32_t *coords, const float *vals, int64_t nnz, c
  * With any host pointer the call returns when `out` is complete; with device
  * pointers only it is asynchronous on `stream`.
  * Errors: BLCO_ERR_ARG, BLCO_ERR_UNSUPPORTED (rank), BLCO_ERR_OOM (staging),
+ * BLCO_ERR_STATE (a store built with float64 values: blco_mttkrp_f64),
  * BLCO_ERR_CUDA.
  */
 blco_status blco_mttkrp(blco_handle h, int mode, const void *const *factors, blco_dtype fdt, int R,
