@@ -290,7 +290,7 @@ def cpu_baseline_leg(spec, c_h, v_h, A):
     Af = [a.cpu().numpy().astype(np.float64) for a in A]
     cores = os.cpu_count() or 1
     lines = []
-    for label, sample, fn in (("all cores", 20_000_000, "rows"), ("one core", 5_000_000, "plain")):
+    for label, sample, fn in (("all cores", 50_000_000, "rows"), ("one core", 5_000_000, "plain")):
         n = min(spec.nnz, sample, c_h.shape[0])
         c = c_h[:n]
         v = v_h[:n].astype(np.float64)
