@@ -63,8 +63,8 @@ FP32_TOL, BF16_TOL = 1e-5, 1e-2
 # (profiles/), valid only for the kernel source it was taken from (sha256 of
 # the kernel header and its float32 translation unit): workload -> record.
 TRAFFIC_RECORDS = {
-    "zipf1.1-4d-500M": {"src_sha256": "84f2d702736a96d53f1cfa0ff02524c674ad35023ac4a7f99839c1dcba10d5e1",
-                        "bytes_per_launch": 7.204e9},  # mean of modes 0-3, R = 32, float32 factors
+    "zipf1.1-4d-500M": {"src_sha256": "018f32bfb77f4f82e8a396ed779b77d8b1807173beb832e3e2ffb5035b6276a4",
+                        "bytes_per_launch": 7.210e9},  # mean of modes 0-3, R = 32, float32 factors
 }
 
 
@@ -82,6 +82,8 @@ def parse_args(argv=None):
     p.add_argument("--no-errors", action="store_true")
     p.add_argument("--no-extras", action="store_true")
     p.add_argument("--nnz", type=int, default=0, help="override the nonzero count (profiling captures only)")
+    p.add_argument("--resident", action="store_true",
+                   help="keep the store on the device for a workload that streams (profiling captures only)")
     return p.parse_args(argv)
 
 
@@ -191,12 +193,12 @@ def hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def mttkrp_src_sha() -> str:
-    """sha256 over the MTTKRP kernel's sources (the kernel header and its
-    float32 translation unit), to tell whether a recorded ncu traffic figure
-    still describes the kernel being timed."""
+def mttkrp_src_sha(onepass: bool = False) -> str:
+    """sha256 over the MTTKRP kernel's sources (the kernel header and the
+    float32 translation unit, or the one-pass kernel's unit), to tell whether
+    a recorded ncu traffic figure still describes the kernel being timed."""
     h = hashlib.sha256()
-    for name in ("mttkrp_kernels.cuh", "mttkrp_f32.cu"):
+    for name in ("mttkrp_kernels.cuh", "mttkrp_fused.cu" if onepass else "mttkrp_f32.cu"):
         with open(os.path.join(ROOT, "paper_2201_12523_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
@@ -213,6 +215,20 @@ def algorithmic_bytes(spec, R: int, fbytes: int, mode: int, rows=None) -> int:
         if k != mode:
             b += d * R * fbytes
     return b
+
+
+def onepass_bytes(spec, R: int, fbytes: int, rows=None) -> int:
+    """Compulsory bytes of one all-mode launch of the one-pass kernel (5-mode
+    stores): the key/value stream once, every factor matrix once, every
+    float32 output once."""
+    rows = rows or spec.dims
+    return 12 * spec.nnz + sum(d * R * (fbytes + 4) for d in rows)
+
+
+def mttkrp_kind(prof) -> str:
+    """Profile kind of the MTTKRP kernel an all-mode step ran: the one-pass
+    kernel (5-mode stores) or the per-mode kernel."""
+    return "mttkrp_all_fused" if prof.get("mttkrp_all_fused", (0, 0.0))[0] else "mttkrp"
 
 
 def gen_inputs(spec, device):
@@ -399,7 +415,7 @@ def measure_mttkrp(blco, spec, args, ranks, dev, steps, warmup, *, headline, sam
     torch.cuda.synchronize()
     gen_s = time.perf_counter() - t_gen
     torch.cuda.empty_cache()
-    budget = STREAMED.get(spec.name.split("@")[0], 0)
+    budget = 0 if args.resident else STREAMED.get(spec.name.split("@")[0], 0)
     eb0, eb1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     eb0.record(stream)
     t = blco.Tensor.build(coords, vals, spec.dims, device_budget_bytes=budget, force_stream=bool(budget))
@@ -445,14 +461,24 @@ def measure_mttkrp(blco, spec, args, ranks, dev, steps, warmup, *, headline, sam
            "ms_per_step": ms_max / steps, "value": ranks.rate(spec.nnz * steps, ms / 1e3),
            "unit": "nnz/s (all-mode)", "gen_s": gen_s}
     peak, peak_src = hbm_peak()
-    b32 = sum(algorithmic_bytes(spec, R, 4, n) for n in range(spec.order)) / spec.order
-    ach, kms, kl = kernel_roofline(prof, "mttkrp", b32, peak)
-    touched_bytes = sum(algorithmic_bytes(spec, R, 4, n, touched) for n in range(spec.order)) / spec.order
+    kind = mttkrp_kind(prof)
+    onepass = kind == "mttkrp_all_fused"
+    if onepass:
+        b32 = onepass_bytes(spec, R, 4)
+        touched_bytes = onepass_bytes(spec, R, 4, touched)
+        kname = f"k_mttkrp_fused<float,{R},{spec.order}>"
+    else:
+        b32 = sum(algorithmic_bytes(spec, R, 4, n) for n in range(spec.order)) / spec.order
+        touched_bytes = sum(algorithmic_bytes(spec, R, 4, n, touched) for n in range(spec.order)) / spec.order
+        kname = f"k_mttkrp<float,{R},{spec.order - 1}>"
+    ach, kms, kl = kernel_roofline(prof, kind, b32, peak)
     rec = TRAFFIC_RECORDS.get(spec.name)
-    traffic = rec["bytes_per_launch"] if rec and rec["src_sha256"] == mttkrp_src_sha() else None
+    traffic = rec["bytes_per_launch"] if rec and rec["src_sha256"] == mttkrp_src_sha(onepass) else None
     res["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                        "frac": (ach / peak) if ach else None, "traffic": traffic,
-                       "kernel": f"k_mttkrp<float,{R},{spec.order - 1}>",
+                       "kernel": kname,
+                       "launch": "one launch per all-mode step (every mode in one pass)" if onepass
+                       else "one launch per mode",
                        "peak_source": peak_src + " (burst copy, MEASURED_PEAKS hbm_gbs)",
                        "algorithmic_bytes_per_launch": b32, "ms_per_launch": kms,
                        "touched_rows_per_mode": touched, "algorithmic_bytes_touched_rows": touched_bytes,
@@ -486,7 +512,7 @@ def measure_mttkrp(blco, spec, args, ranks, dev, steps, warmup, *, headline, sam
         blco.blco_profile_enable(t_res.handle, True)
         ms_r = ranks.max(time_steps(step_r, steps, stream)) / steps
         blco.blco_profile_enable(t_res.handle, False)
-        ach_r, kms_r, _ = kernel_roofline(blco.blco_profile_read(t_res.handle), "mttkrp", b32, peak)
+        ach_r, kms_r, _ = kernel_roofline(blco.blco_profile_read(t_res.handle), kind, b32, peak)
         if ach_r:
             # batches of the streamed store overlap on the queue streams, so their
             # launch durations say little; a resident launch covers the whole store
@@ -515,8 +541,9 @@ def measure_mttkrp(blco, spec, args, ranks, dev, steps, warmup, *, headline, sam
         ms16 = ranks.max(time_steps(step16, steps, stream))
         blco.blco_profile_enable(t.handle, False)
         p16 = blco.blco_profile_read(t.handle)
-        b16 = sum(algorithmic_bytes(spec, R, 2, n) for n in range(spec.order)) / spec.order
-        ach16, kms16, _ = kernel_roofline(p16, "mttkrp", b16, peak)
+        b16 = onepass_bytes(spec, R, 2) if onepass else \
+            sum(algorithmic_bytes(spec, R, 2, n) for n in range(spec.order)) / spec.order
+        ach16, kms16, _ = kernel_roofline(p16, kind, b16, peak)
         res["bf16"] = {"value": ranks.rate(spec.nnz * steps, ms16 / 1e3), "ms_per_step": ms16 / steps,
                        "speedup_vs_f32": ms_max / ms16, "ms_per_launch": kms16,
                        "roofline_frac": (ach16 / peak) if ach16 else None,

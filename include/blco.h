@@ -158,6 +158,11 @@ blco_status blco_mttkrp(blco_handle h, int mode, const void *const *factors, blc
  * link once per call: while it sits in its queue's reservation the kernels
  * of every requested mode run on it (Section 4.2); the factors and all the
  * requested outputs stay on the device meanwhile.
+ * A 5-mode store (every I_n <= 2^24, R = 16, 32 or 64) is computed in one
+ * pass: each nonzero's five factor rows are gathered once and its product
+ * goes to every requested output (Eq. 1 for all modes at once), one kernel
+ * launch per call (per batch when streamed). Other stores run the per-mode
+ * kernels; the results agree within float32 rounding either way.
  */
 blco_status blco_mttkrp_all(blco_handle h, const void *const *factors, blco_dtype fdt, int R,
                             float *const *outs, blco_stream stream);

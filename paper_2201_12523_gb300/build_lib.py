@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libblco.so")
-SOURCES = ["api.cu", "build.cu", "mttkrp.cu", "mttkrp_f32.cu", "mttkrp_bf16.cu", "mttkrp_f16.cu", "mttkrp_f64.cu",
+SOURCES = ["api.cu", "build.cu", "mttkrp.cu", "mttkrp_f32.cu", "mttkrp_bf16.cu", "mttkrp_f16.cu", "mttkrp_fused.cu", "mttkrp_f64.cu",
            "dense.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -940,16 +940,18 @@ cudaError_t copy_streams(blco_tensor *h) {
     return e;
 }
 
-// All-mode MTTKRP of a streamed store (Section 4.2): every batch of blocks
-// crosses the host link once per call, and while it sits in its queue's
-// reservation the kernels of all requested modes run on it, one after
-// another on the queue's stream. Host arguments are staged in the
-// workspace: factors uploaded on `s` first, results downloaded at the end.
-// Short modes accumulate straight into their outputs here (no private
-// copies: their buffer holds one mode at a time).
-static blco_status mttkrp_all_streamed(blco_tensor *h, FactorSet fs, const bool *host_in, const bool *host_out,
+// All-mode MTTKRP in one pass over the store: on a streamed store every
+// batch of blocks crosses the host link once per call (Section 4.2), and
+// while it sits in its queue's reservation either the fused all-mode kernel
+// (`fused`: each nonzero's N rows gathered once for every mode) or the
+// kernels of all requested modes, one after another, run on it; on a
+// resident store the same launches run once over the whole store. Host
+// arguments are staged in the workspace: factors uploaded on `s` first,
+// results downloaded at the end. Short modes accumulate straight into their
+// outputs here (no private copies: their buffer holds one mode at a time).
+static blco_status mttkrp_all_onepass(blco_tensor *h, FactorSet fs, const bool *host_in, const bool *host_out,
                                        const size_t *in_off, const size_t *out_off, size_t total, blco_dtype fdt, int R,
-                                       float *const *outs, cudaStream_t s) {
+                                       float *const *outs, cudaStream_t s, bool fused) {
     const int N = h->L.N;
     char *base = nullptr;
     if (total > 0) {
@@ -976,7 +978,18 @@ static blco_status mttkrp_all_streamed(blco_tensor *h, FactorSet fs, const bool 
         if (e != cudaSuccess) return cuda_fail(e, "zero output");
     }
     const OutCopies one;
+    HotRows hot_all[MAXN];
+    for (int n = 0; n < N; ++n) {
+        hot_all[n].rows = h->d_hot[n];
+        hot_all[n].count = h->hot_count[n];
+        hot_all[n].dense = 0;
+    }
+    float *dst_all[MAXN] = {};
+    for (int n = 0; n < N; ++n) dst_all[n] = outs[n] ? dst[n] : nullptr;
     blco_status st = over_store(h, nullptr, nullptr, s, [&](const StoreView &sv, cudaStream_t q) {
+        if (fused)
+            return timed(h, "mttkrp_all_fused", q,
+                         [&]() { return launch_mttkrp_fused(sv, fs, fdt, R, hot_all, dst_all, q); });
         for (int n = 0; n < N; ++n) {
             if (!outs[n]) continue;
             cudaError_t e = timed(h, "mttkrp", q, [&]() {
@@ -1032,7 +1045,9 @@ blco_status blco_mttkrp_all(blco_handle h, const void *const *factors, blco_dtyp
     }
     FactorSet fs;
     for (int k = 0; k < MAXN; ++k) fs.ptr[k] = k < N ? factors[k] : nullptr;
-    if (h->streamed) return mttkrp_all_streamed(h, fs, host_in, host_out, in_off, out_off, total, fdt, R, outs, s);
+    const bool fused = fused_supported(h->view(), R);
+    if (fused || h->streamed)
+        return mttkrp_all_onepass(h, fs, host_in, host_out, in_off, out_off, total, fdt, R, outs, s, fused);
     if (total == 0) {  // device arguments: the modes one after another on s
         for (int n = 0; n < N; ++n) {
             if (!outs[n]) continue;

@@ -94,6 +94,13 @@ cudaError_t launch_cp_fwd_bf16(const StoreView &sv, const FactorSet &fs, int R, 
 cudaError_t launch_cp_fwd_f16(const StoreView &sv, const FactorSet &fs, int R, float *xhat, int64_t xorigin,
                               cudaStream_t s);
 bool rank_supported(int R);
+// All-mode MTTKRP in one pass (mttkrp_fused.cu): outs[n] for every mode with
+// outs[n] != NULL; hot: per-mode hot rows. fused_supported tells whether the
+// store's shape and the rank allow it (5 modes, every I_n <= 2^24,
+// R = 16, 32 or 64).
+bool fused_supported(const StoreView &sv, int R);
+cudaError_t launch_mttkrp_fused(const StoreView &sv, const FactorSet &fs, blco_dtype fdt, int R, const HotRows *hot,
+                                float *const *outs, cudaStream_t s);
 // mttkrp_f64.cu: float64 values, factors and output
 cudaError_t launch_mttkrp_f64(const StoreView &sv, const double *const *factors, int R, int mode, const HotRows &hot,
                               double *out, cudaStream_t s);

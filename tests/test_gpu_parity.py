@@ -87,6 +87,36 @@ def test_empty_and_single():
     assert np.count_nonzero(M[:4]) == 0
 
 
+@pytest.mark.parametrize("R", [16, 64])
+def test_empty_and_single_five_modes_one_pass(R):
+    """The one-pass all-mode kernel on an empty 5-mode store (outputs zeroed,
+    no launch) and on a single nonzero (every mode's row is the product of
+    the other four rows, every other row zero), also with a streamed store."""
+    dims = (5, 6, 7, 3, 1 << 20)
+    A = [torch.randn(d, R, device="cuda") for d in dims]
+    t = blco.Tensor.build(torch.zeros((0, 5), dtype=torch.int32, device="cuda"), torch.zeros(0, device="cuda"), dims)
+    outs = [torch.full((d, R), 7.0, device="cuda") for d in dims]
+    t.mttkrp_all(A, outs=outs)
+    torch.cuda.synchronize()
+    assert all(torch.count_nonzero(o) == 0 for o in outs)
+    c = torch.tensor([[4, 5, 6, 2, (1 << 20) - 1]], dtype=torch.int32, device="cuda")
+    v = torch.tensor([-1.5], device="cuda")
+    for kw in ({}, dict(force_stream=True)):
+        t1 = blco.Tensor.build(c, v, dims, **kw)
+        outs = t1.mttkrp_all(A)
+        torch.cuda.synchronize()
+        rows = c[0].tolist()
+        for n in range(5):
+            ref = torch.full((R,), -1.5, dtype=torch.float64, device="cuda")
+            for k in range(5):
+                if k != n:
+                    ref *= A[k][rows[k]].double()
+            np.testing.assert_allclose(outs[n][rows[n]].double().cpu().numpy(), ref.cpu().numpy(), rtol=1e-6)
+            other = torch.ones(dims[n], dtype=torch.bool, device="cuda")
+            other[rows[n]] = False
+            assert torch.count_nonzero(outs[n][other]) == 0
+
+
 def test_out_of_range_coordinate_is_index_error():
     c = torch.tensor([[0, 0, 0], [1, 6, 0], [2, 1, 1]], dtype=torch.int32, device="cuda")
     v = torch.ones(3, device="cuda")
@@ -293,13 +323,15 @@ def test_streamed_store_matches(nq):
     _store_equal(t, coords, vals, spec.dims, 64, 4000)
 
 
-@pytest.mark.parametrize("nq", [1, 3])
-def test_streamed_all_mode_uploads_each_batch_once(nq):
+@pytest.mark.parametrize("order,nq", [(5, 1), (5, 3), (4, 2)])
+def test_streamed_all_mode_uploads_each_batch_once(order, nq):
     """All-mode MTTKRP of a streamed store: each batch of blocks crosses the
     host link once per call (Section 4.2's queues), and every mode's kernel
-    runs on it while it is resident; the results match the oracle, also for
-    a short R = 64 mode and with bf16 factors."""
-    spec = synth.small(3, 150_000, (1 << 24, 1 << 20, 1 << 16, 1 << 12, 1 << 8))
+    runs on it while it is resident (5 modes: one one-pass launch per batch;
+    4 modes: one per-mode launch per batch and mode); the results match the
+    oracle, also for a short R = 64 mode and with bf16 factors."""
+    dims = (1 << 24, 1 << 20, 1 << 16, 1 << 12, 1 << 8)[:order]
+    spec = synth.small(3 if order == 5 else 2, 150_000, dims)
     coords, vals, _ = make(spec)
     t = blco.Tensor.build(coords, vals, spec.dims, force_stream=True, max_nnz_per_block=4000, n_queues=nq)
     c = coords.cpu().numpy()
@@ -318,8 +350,11 @@ def test_streamed_all_mode_uploads_each_batch_once(nq):
         batches = one["upload"][0]
         assert batches > 1
         assert allm["upload"][0] == batches
-        assert allm["mttkrp"][0] == batches * 5
-        for n in range(5):
+        if order == 5:
+            assert allm["mttkrp_all_fused"][0] == batches
+        else:
+            assert allm["mttkrp"][0] == batches * order
+        for n in range(order):
             M, S = oracle.mttkrp(c, v, spec.dims, Aref, n)
             assert oracle.max_rel_err(outs[n].cpu().numpy(), M, S) <= FP32_TOL, (R, dt, n)
 
@@ -425,6 +460,72 @@ def test_partitioned_mttkrp_sums_to_the_full_result(parts):
     with pytest.raises(blco.BlcoError) as ei:
         blco.blco_mttkrp_range(ts.handle, 0, 0, 64, A, blco.BLCO_F32, R, out)
     assert ei.value.status == blco.BLCO_ERR_STATE
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16, torch.float16])
+@pytest.mark.parametrize("R", [16, 32, 64])
+@pytest.mark.parametrize("which", ["5d", "5d-blocked", "5d-short"])
+def test_all_mode_one_pass_matches_oracle(which, R, dtype):
+    """blco_mttkrp_all on a 5-mode store gathers each nonzero's rows once for
+    every mode (one kernel launch): every mode against the FP64 oracle, with
+    ragged tails, a blocked store with 2^24-row modes, modes short enough to
+    be held on chip whole, and a mode left out."""
+    if which == "5d":
+        spec = synth.small(3, 60_013, (1 << 12, 1 << 10, 1 << 9, 1 << 6, 1 << 4))
+        kw = {}
+    elif which == "5d-blocked":
+        spec = synth.small(3, 40_009, (1 << 24, 1 << 20, 1 << 16, 1 << 12, 1 << 8))
+        kw = dict(max_nnz_per_block=5000)
+    else:
+        spec = synth.small(3, 20_011, (400, 9, 5, 3, 2))
+        kw = {}
+    coords, vals, _ = make(spec)
+    A = synth.factors(spec, rank=R, device="cuda", dist="normal")
+    F = A if dtype == torch.float32 else [blco.convert(a, dtype) for a in A]
+    Aref = to_np64(A) if dtype == torch.float32 else rounded16(A, dtype)
+    t = blco.Tensor.build(coords, vals, spec.dims, **kw)
+    c = coords.cpu().numpy()
+    v = vals.cpu().numpy().astype(np.float64)
+    blco.blco_profile_enable(t.handle, True)
+    outs = t.mttkrp_all(F)
+    torch.cuda.synchronize()
+    prof = blco.blco_profile_read(t.handle)
+    blco.blco_profile_enable(t.handle, False)
+    assert prof["mttkrp_all_fused"][0] == 1 and "mttkrp" not in prof
+    for n in range(spec.order):
+        M, S = oracle.mttkrp(c, v, spec.dims, Aref, n)
+        assert oracle.max_rel_err(outs[n].cpu().numpy(), M, S) <= FP32_TOL, n
+    # mode 1 left out (a NULL output): the other modes exact as before
+    outs2 = [torch.empty((d, R), device="cuda") for d in spec.dims]
+    outs2[1] = None
+    blco.blco_mttkrp_all(t.handle, F, blco._fdt(F), R, outs2)
+    torch.cuda.synchronize()
+    for n in (0, spec.order - 1):
+        M, S = oracle.mttkrp(c, v, spec.dims, Aref, n)
+        assert oracle.max_rel_err(outs2[n].cpu().numpy(), M, S) <= FP32_TOL, n
+
+
+@pytest.mark.parametrize("dims,R", [((1 << 12, 1 << 10, 1 << 9), 32), ((1 << 11, 1 << 10, 1 << 8, 1 << 5), 16),
+                                    ((1 << 10, 1 << 9, 1 << 8, 1 << 6, 1 << 4), 8)])
+def test_all_mode_per_mode_kernels(dims, R):
+    """blco_mttkrp_all where the one-pass kernel does not apply (3 and 4
+    modes; a rank it is not built for): one per-mode launch per requested
+    mode, every mode against the oracle."""
+    spec = synth.small(1 if len(dims) == 3 else (2 if len(dims) == 4 else 3), 50_021, dims)
+    coords, vals, _ = make(spec)
+    A = synth.factors(spec, rank=R, device="cuda", dist="normal")
+    t = blco.Tensor.build(coords, vals, spec.dims)
+    blco.blco_profile_enable(t.handle, True)
+    outs = t.mttkrp_all(A)
+    torch.cuda.synchronize()
+    prof = blco.blco_profile_read(t.handle)
+    blco.blco_profile_enable(t.handle, False)
+    assert prof["mttkrp"][0] == len(dims) and "mttkrp_all_fused" not in prof
+    c = coords.cpu().numpy()
+    v = vals.cpu().numpy().astype(np.float64)
+    for n in range(len(dims)):
+        M, S = oracle.mttkrp(c, v, spec.dims, to_np64(A), n)
+        assert oracle.max_rel_err(outs[n].cpu().numpy(), M, S) <= FP32_TOL, n
 
 
 @pytest.mark.parametrize("R", [8, 16, 32, 64])
