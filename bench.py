@@ -432,6 +432,10 @@ def measure_mttkrp(blco, spec, args, ranks, dev, steps, warmup, *, headline, sam
     # a streamed workload is also timed on a store resident on the device: the
     # same all-mode MTTKRP without the host link
     t_res = blco.Tensor.build(coords, vals, spec.dims) if info["streamed"] else None
+    # ... and on a streamed store whose kernels read it in pinned host memory
+    # (build option host_reads: no device queues or batch copies)
+    t_hr = (blco.Tensor.build(coords, vals, spec.dims, device_budget_bytes=budget, force_stream=True, host_reads=True)
+            if info["streamed"] else None)
     need_host = headline and (not args.no_errors or not args.no_cpu) and ranks.rank == 0
     c_h = coords.cpu().numpy().view(np.uint32) if need_host else None
     v_h = vals.cpu().numpy() if need_host else None
@@ -530,6 +534,22 @@ def measure_mttkrp(blco, spec, args, ranks, dev, steps, warmup, *, headline, sam
         res["host_link"]["bound"] = ("kernels: the all-mode MTTKRP of a resident store takes %.0f ms, longer than "
                                      "the %.0f ms the host link needs for the store at its measured peak" % (ms_r, link_ms)
                                      if ms_r > link_ms else "host link")
+        # the same step with the kernel reading the store in host memory
+        outs_h = [torch.empty_like(o) for o in outs]
+        step_h = make_step(A, t_hr, outs_h)
+        for _ in range(warmup):
+            step_h()
+        ms_h = ranks.max(time_steps(step_h, steps, stream)) / steps
+        ih = t_hr.info()
+        ach_h = moved / (ms_h / 1e3) / 1e9
+        res["host_reads"] = {"ms_per_step": ms_h, "value": ranks.rate(spec.nnz, ms_h / 1e3),
+                             "unit": "nnz/s (all-mode)", "host_link_achieved": ach_h, "host_link_frac": ach_h / link,
+                             "device_bytes": ih["device_bytes"], "host_bytes": ih["host_bytes"],
+                             "note": "build option host_reads: one all-mode launch loads the store's keys and values "
+                                     "from pinned host memory over the host link; no device queues or batch copies"}
+        t_hr.destroy()
+        t_hr = None
+        del outs_h
 
     # bfloat16 factors, same step; Kahan-compensated run sums on the second store
     err_results = {}

@@ -82,6 +82,21 @@ typedef struct {
                                     rounding per run instead of one per term; the
                                     measured errors at the benchmark sizes are the
                                     same, and the plain sums are 8-10% faster) */
+    int32_t host_reads;          /* streamed stores only: 1 = the kernels read the
+                                    store's keys and values straight from its
+                                    pinned host memory over the host link (one
+                                    launch over the whole store; no device queues,
+                                    no batch copies, no queue reservations in
+                                    device memory). 0 (default) = the paper's
+                                    scheme: batches of blocks copied into device
+                                    queues on a side stream, overlapped with the
+                                    kernels (Section 4.2). On a coherent host link
+                                    (NVLink-C2C) the GPU's loads read pinned host
+                                    memory at the link's copy rate. An all-mode
+                                    call with the per-mode kernels (stores of
+                                    other than 5 modes) reads the store once per
+                                    mode this way, against once per call through
+                                    the queues */
 } blco_build_opts;
 
 typedef struct {
@@ -102,6 +117,7 @@ typedef struct {
                                               of them on chip) */
     int64_t device_bytes;                  /* device memory held by the handle */
     int64_t host_bytes;                    /* pinned host memory held by the handle */
+    int32_t host_reads;                    /* 1 if kernels read the streamed store in host memory */
 } blco_info_t;
 
 /* Fills *opts with the defaults. Returns BLCO_ERR_ARG for a null pointer. */
@@ -184,7 +200,8 @@ blco_status blco_mttkrp_all(blco_handle h, const void *const *factors, blco_dtyp
  *     = the mode-`mode` MTTKRP of the nonzeros at store positions
  *     [begin, end); begin a multiple of 32, 0 <= begin <= end <= nnz. Other
  *     arguments as blco_mttkrp. The store must be resident on the device
- *     (BLCO_ERR_STATE for a streamed store).
+ *     or read in host memory (host_reads; BLCO_ERR_STATE for a store
+ *     streamed through the device queues).
  * Errors: BLCO_ERR_ARG, BLCO_ERR_STATE, BLCO_ERR_UNSUPPORTED, BLCO_ERR_OOM,
  * BLCO_ERR_CUDA.
  */

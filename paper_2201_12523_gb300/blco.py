@@ -41,7 +41,7 @@ EXPORTS = ["blco_default_opts", "blco_build", "blco_mttkrp", "blco_mttkrp_all", 
 class BuildOpts(ctypes.Structure):
     _fields_ = [("max_nnz_per_block", ctypes.c_int64), ("line_bits", ctypes.c_int32), ("n_queues", ctypes.c_int32),
                 ("device_budget_bytes", ctypes.c_int64), ("force_stream", ctypes.c_int32),
-                ("compensated_sums", ctypes.c_int32)]
+                ("compensated_sums", ctypes.c_int32), ("host_reads", ctypes.c_int32)]
 
 
 class ProfileEntry(ctypes.Structure):
@@ -55,7 +55,7 @@ class Info(ctypes.Structure):
                 ("streamed", ctypes.c_int32), ("nblocks", ctypes.c_int64), ("max_nnz_per_block", ctypes.c_int64),
                 ("queue_nnz", ctypes.c_int64), ("n_queues", ctypes.c_int32),
                 ("hot_rows", ctypes.c_int32 * MAX_MODES), ("device_bytes", ctypes.c_int64),
-                ("host_bytes", ctypes.c_int64)]
+                ("host_bytes", ctypes.c_int64), ("host_reads", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         N = self.order
@@ -64,7 +64,8 @@ class Info(ctypes.Structure):
                 "line_bits": self.line_bits, "streamed": bool(self.streamed), "nblocks": self.nblocks,
                 "max_nnz_per_block": self.max_nnz_per_block, "queue_nnz": self.queue_nnz,
                 "n_queues": self.n_queues, "hot_rows": list(self.hot_rows[:N]),
-                "device_bytes": self.device_bytes, "host_bytes": self.host_bytes}
+                "device_bytes": self.device_bytes, "host_bytes": self.host_bytes,
+                "host_reads": bool(self.host_reads)}
 
 
 def _load():
@@ -337,7 +338,7 @@ class Tensor:
     @classmethod
     def build(cls, coords, vals, dims: Sequence[int], *, max_nnz_per_block: int = 0, line_bits: int = 0,
               n_queues: int = 0, device_budget_bytes: int = 0, force_stream: bool = False,
-              compensated_sums: bool = False, stream=None) -> "Tensor":
+              compensated_sums: bool = False, host_reads: bool = False, stream=None) -> "Tensor":
         o = blco_default_opts()
         if max_nnz_per_block:
             o.max_nnz_per_block = int(max_nnz_per_block)
@@ -348,6 +349,7 @@ class Tensor:
         o.device_budget_bytes = int(device_budget_bytes)
         o.force_stream = 1 if force_stream else 0
         o.compensated_sums = 1 if compensated_sums else 0
+        o.host_reads = 1 if host_reads else 0
         if getattr(vals, "dtype", None) in (torch.float64, np.float64):
             return cls(blco_build_f64(coords, vals, dims, o, stream), dims)
         return cls(blco_build(coords, vals, dims, o, stream), dims)

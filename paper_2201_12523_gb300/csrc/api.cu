@@ -87,6 +87,7 @@ struct blco_tensor {
     int nq = 8;
     int64_t budget = 0;
     bool streamed = false;
+    bool host_reads = false;   // streamed store read in host memory by the kernels (no queues)
     bool compensated = false;  // 16-bit factors: Kahan-compensated run sums (build option)
     // store (device when resident, pinned host when streamed)
     uint64_t *d_keys = nullptr;
@@ -97,6 +98,8 @@ struct blco_tensor {
     uint64_t *h_keys = nullptr;
     float *h_vals = nullptr;
     uint32_t *h_perm = nullptr;
+    uint64_t *hd_keys = nullptr;  // device views of h_keys / h_vals (host_reads)
+    float *hd_vals = nullptr;
     // block table
     std::vector<int64_t> bstart;
     std::vector<uint32_t> bhigh;
@@ -331,10 +334,16 @@ blco_status over_store(blco_tensor *h, const char *name, const float *vals_ext, 
         return timed(h, name, q, [&]() { return launch_fn(sv, q); });
     };
     if (h->nnz == 0) return BLCO_OK;
-    if (!h->streamed) {
+    if (!h->streamed || h->host_reads) {
+        // resident, or read in pinned host memory by the kernel itself: one
+        // launch over the store (or the requested part of it)
         StoreView sv = h->view();
+        if (h->host_reads) {
+            sv.keys = h->hd_keys;
+            sv.vals = h->hd_vals;
+        }
         if (vals_ext) sv.vals = vals_ext;
-        if (range_end >= 0) {  // a part of the store (resident stores only)
+        if (range_end >= 0) {  // a part of the store
             sv.begin = range_begin;
             sv.end = range_end;
             if (sv.end <= sv.begin) return BLCO_OK;
@@ -533,6 +542,7 @@ static blco_status build_impl(const uint32_t *coords, const float *vals, int64_t
         o.device_budget_bytes = opts->device_budget_bytes;
         o.force_stream = opts->force_stream;
         o.compensated_sums = opts->compensated_sums;
+        o.host_reads = opts->host_reads;
     }
     blco_tensor *h = new blco_tensor();
     h->L.N = N;
@@ -644,8 +654,9 @@ static blco_status build_impl(const uint32_t *coords, const float *vals, int64_t
         if (o.force_stream || over) {
             h->streamed = true;
             h->queue_nnz = ((std::max(maxblk, std::min(h->max_nnz, nnz)) + 31) / 32) * 32;
-            e = cudaHostAlloc((void **)&h->h_keys, sizeof(uint64_t) * h->npad, cudaHostAllocDefault);
-            if (e == cudaSuccess) e = cudaHostAlloc((void **)&h->h_vals, sizeof(float) * h->npad, cudaHostAllocDefault);
+            // mapped: with host_reads the kernels load keys and values from here
+            e = cudaHostAlloc((void **)&h->h_keys, sizeof(uint64_t) * h->npad, cudaHostAllocMapped);
+            if (e == cudaSuccess) e = cudaHostAlloc((void **)&h->h_vals, sizeof(float) * h->npad, cudaHostAllocMapped);
             if (e == cudaSuccess) e = cudaHostAlloc((void **)&h->h_perm, sizeof(uint32_t) * std::max<int64_t>(nnz, 1), cudaHostAllocDefault);
             if (e == cudaSuccess) e = cudaMemcpyAsync(h->h_keys, h->d_keys, sizeof(uint64_t) * h->npad, cudaMemcpyDeviceToHost, s);
             if (e == cudaSuccess) e = cudaMemcpyAsync(h->h_vals, h->d_vals, sizeof(float) * h->npad, cudaMemcpyDeviceToHost, s);
@@ -660,30 +671,45 @@ static blco_status build_impl(const uint32_t *coords, const float *vals, int64_t
             h->d_vals = nullptr;
             h->d_perm = nullptr;
             h->dev_bytes -= store_bytes;
-            // queues: as many as the budget allows (at least one)
-            const int64_t qbytes = h->queue_nnz * 12;
-            while (h->nq > 1 && h->budget > 0 && h->dev_bytes + h->nq * qbytes > h->budget) h->nq--;
-            if (h->budget > 0 && h->dev_bytes + h->nq * qbytes > h->budget)
-                BAIL(fail(BLCO_ERR_OOM, "device budget cannot hold one queue reservation; lower max_nnz_per_block"));
-            h->building = false;
-            for (int q = 0; q < h->nq && e == cudaSuccess; ++q) {
-                e = h->dalloc((void **)&h->q_keys[q], sizeof(uint64_t) * h->queue_nnz);
-                if (e == cudaSuccess) e = h->dalloc((void **)&h->q_vals[q], sizeof(float) * h->queue_nnz);
-                if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->q_stream[q], cudaStreamNonBlocking);
-                if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->q_done[q], cudaEventDisableTiming);
-                if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->q_copied[q], cudaEventDisableTiming);
-            }
-            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
-            if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->q_up, cudaStreamNonBlocking);
-            if (e != cudaSuccess) BAIL(cuda_fail(e, "queue reservation"));
-            // batches: consecutive whole blocks up to the reservation (Section 4.2)
-            int64_t b0 = 0;
-            const int64_t nb = (int64_t)h->bstart.size() - 1;
-            while (b0 < nb) {
-                int64_t b1 = b0 + 1;
-                while (b1 < nb && h->bstart[b1 + 1] - h->bstart[b0] <= h->queue_nnz) ++b1;
-                h->batches.push_back({h->bstart[b0], h->bstart[b1]});
-                b0 = b1;
+            if (o.host_reads) {
+                // the kernels read the store where it is: device views of the
+                // mapped host arrays, no queues or batches
+                h->host_reads = true;
+                h->nq = 0;
+                h->queue_nnz = 0;
+                void *dk = nullptr, *dv = nullptr;
+                e = cudaHostGetDevicePointer(&dk, h->h_keys, 0);
+                if (e == cudaSuccess) e = cudaHostGetDevicePointer(&dv, h->h_vals, 0);
+                if (e != cudaSuccess) BAIL(cuda_fail(e, "device view of the host store"));
+                h->hd_keys = static_cast<uint64_t *>(dk);
+                h->hd_vals = static_cast<float *>(dv);
+                h->building = false;
+            } else {
+                // queues: as many as the budget allows (at least one)
+                const int64_t qbytes = h->queue_nnz * 12;
+                while (h->nq > 1 && h->budget > 0 && h->dev_bytes + h->nq * qbytes > h->budget) h->nq--;
+                if (h->budget > 0 && h->dev_bytes + h->nq * qbytes > h->budget)
+                    BAIL(fail(BLCO_ERR_OOM, "device budget cannot hold one queue reservation; lower max_nnz_per_block"));
+                h->building = false;
+                for (int q = 0; q < h->nq && e == cudaSuccess; ++q) {
+                    e = h->dalloc((void **)&h->q_keys[q], sizeof(uint64_t) * h->queue_nnz);
+                    if (e == cudaSuccess) e = h->dalloc((void **)&h->q_vals[q], sizeof(float) * h->queue_nnz);
+                    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->q_stream[q], cudaStreamNonBlocking);
+                    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->q_done[q], cudaEventDisableTiming);
+                    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->q_copied[q], cudaEventDisableTiming);
+                }
+                if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+                if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->q_up, cudaStreamNonBlocking);
+                if (e != cudaSuccess) BAIL(cuda_fail(e, "queue reservation"));
+                // batches: consecutive whole blocks up to the reservation (Section 4.2)
+                int64_t b0 = 0;
+                const int64_t nb = (int64_t)h->bstart.size() - 1;
+                while (b0 < nb) {
+                    int64_t b1 = b0 + 1;
+                    while (b1 < nb && h->bstart[b1 + 1] - h->bstart[b0] <= h->queue_nnz) ++b1;
+                    h->batches.push_back({h->bstart[b0], h->bstart[b1]});
+                    b0 = b1;
+                }
             }
         } else if (h->budget > 0 && h->dev_bytes > h->budget) {
             BAIL(fail(BLCO_ERR_OOM, "device budget exceeded"));
@@ -894,7 +920,8 @@ blco_status blco_mttkrp_range(blco_handle h, int mode, int64_t begin, int64_t en
     g_err.clear();
     blco_status st = check_common(h, fdt, R);
     if (st != BLCO_OK) return st;
-    if (h->streamed) return fail(BLCO_ERR_STATE, "blco_mttkrp_range needs a store resident on the device");
+    if (h->streamed && !h->host_reads)
+        return fail(BLCO_ERR_STATE, "blco_mttkrp_range needs a store on the device or read in host memory (host_reads)");
     if (mode < 0 || mode >= h->L.N) return fail(BLCO_ERR_ARG, "mode out of range");
     if (begin < 0 || end < begin || end > h->nnz) return fail(BLCO_ERR_ARG, "range outside the store");
     if (begin % 32 != 0) return fail(BLCO_ERR_ARG, "begin must be a multiple of 32");
@@ -1046,7 +1073,10 @@ blco_status blco_mttkrp_all(blco_handle h, const void *const *factors, blco_dtyp
     FactorSet fs;
     for (int k = 0; k < MAXN; ++k) fs.ptr[k] = k < N ? factors[k] : nullptr;
     const bool fused = fused_supported(h->view(), R);
-    if (fused || h->streamed)
+    // a store streamed through the queues crosses the host link once per call
+    // (one pass, every mode on each batch); a store read in host memory runs
+    // the per-mode kernels over it one mode after another, like a resident one
+    if (fused || (h->streamed && !h->host_reads))
         return mttkrp_all_onepass(h, fs, host_in, host_out, in_off, out_off, total, fdt, R, outs, s, fused);
     if (total == 0) {  // device arguments: the modes one after another on s
         for (int n = 0; n < N; ++n) {
@@ -1272,6 +1302,7 @@ blco_status blco_info(blco_handle h, blco_info_t *info) {
     info->n_queues = h->streamed ? h->nq : 0;
     info->device_bytes = h->dev_bytes;
     info->host_bytes = h->host_bytes;
+    info->host_reads = h->host_reads ? 1 : 0;
     return BLCO_OK;
 }
 

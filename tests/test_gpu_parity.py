@@ -125,6 +125,40 @@ def test_out_of_range_coordinate_is_index_error():
     assert ei.value.status == blco.BLCO_ERR_INDEX
 
 
+def _u32_coords(c64):
+    """uint32 coordinates as the int32 tensor the binding passes (same bits)."""
+    return torch.from_numpy(np.ascontiguousarray(c64.astype(np.uint32).view(np.int32)))
+
+
+@pytest.mark.parametrize("dims,line,cap", [
+    ((0xFFFFFFFF,) * 4, 64, 1 << 27),                     # 4 x 32 bits = 128 index bits, 64 block bits
+    ((0xFFFFFFFF, (1 << 31) + 1, 3, 1), 64, 4099),         # two 32-bit modes, a length-1 mode, split blocks
+    ((0xFFFFFFFF, 0xFFFFFFFF), 1, 1 << 27),                # 1-bit line: 63 of 64 bits above it
+])
+def test_store_at_maximum_mode_lengths(dims, line, cap):
+    """The largest mode length the ABI takes (2^32 - 1, coordinates are
+    uint32): every coordinate bit above bit 30 reaches the key, the block
+    table and the re-encoded fields as the definition places it (Section 4.1,
+    Section 4.2), with the first and last index of every mode present."""
+    rng = np.random.default_rng(sum(int(d).bit_length() for d in dims) + line)
+    nnz = 20_011
+    c = np.stack([rng.integers(0, d, nnz, dtype=np.uint64) for d in dims], 1)
+    c[0] = 0
+    c[1] = [d - 1 for d in dims]
+    c[2] = [d - 1 if k % 2 else 0 for k, d in enumerate(dims)]
+    coords = _u32_coords(c)
+    vals = torch.from_numpy(rng.random(nnz).astype(np.float32))
+    t = blco.Tensor.build(coords.cuda(), vals.cuda(), dims, line_bits=line, max_nnz_per_block=cap)
+    assert t.info()["total_bits"] == sum(max(int(d - 1).bit_length(), 0) for d in dims)
+    _store_equal(t, coords, vals, dims, line, cap)
+    # the one index past the end of a 2^32 - 1 mode is rejected
+    bad = c[:3].copy()
+    bad[2, 0] = 0xFFFFFFFF
+    with pytest.raises(blco.BlcoError) as ei:
+        blco.Tensor.build(_u32_coords(bad).cuda(), vals[:3].cuda(), dims)
+    assert ei.value.status == blco.BLCO_ERR_INDEX
+
+
 # ------------------------------------------------------------ MTTKRP
 @pytest.mark.parametrize("R", [8, 16, 32, 64, 128])
 def test_mttkrp_uniform_all_ranks(R):
@@ -357,6 +391,50 @@ def test_streamed_all_mode_uploads_each_batch_once(order, nq):
         for n in range(order):
             M, S = oracle.mttkrp(c, v, spec.dims, Aref, n)
             assert oracle.max_rel_err(outs[n].cpu().numpy(), M, S) <= FP32_TOL, (R, dt, n)
+
+
+@pytest.mark.parametrize("order", [3, 5])
+def test_store_read_in_host_memory(order):
+    """A streamed store whose kernels read keys and values in its pinned host
+    memory (build option host_reads): no queue reservations in device memory,
+    the same store bytes, and every call against the oracle -- per-mode
+    MTTKRP, the all-mode call (one pass at 5 modes, per-mode kernels at 3),
+    parts of the store, the CP model and its adjoint."""
+    dims = (1 << 24, 1 << 20, 1 << 16, 1 << 12, 1 << 8) if order == 5 else (1 << 14, 1 << 13, 1 << 7)
+    spec = synth.small(3 if order == 5 else 1, 60_013, dims)
+    coords, vals, A = make(spec)
+    t = blco.Tensor.build(coords, vals, spec.dims, force_stream=True, host_reads=True, max_nnz_per_block=4000)
+    info = t.info()
+    assert info["streamed"] and info["host_reads"] and info["n_queues"] == 0 and info["nblocks"] > 3
+    # the device holds what a queue-streamed store holds, less its queue reservations
+    iq = blco.Tensor.build(coords, vals, spec.dims, force_stream=True, max_nnz_per_block=4000).info()
+    assert info["device_bytes"] + iq["n_queues"] * iq["queue_nnz"] * 12 == iq["device_bytes"]
+    _store_equal(t, coords, vals, spec.dims, 64, 4000)
+    check_mttkrp_all(t, coords, vals, A, spec.dims)
+    c = coords.cpu().numpy()
+    v = vals.cpu().numpy().astype(np.float64)
+    Af = to_np64(A)
+    outs = t.mttkrp_all(A)
+    torch.cuda.synchronize()
+    for n in range(order):
+        M, S = oracle.mttkrp(c, v, spec.dims, Af, n)
+        assert oracle.max_rel_err(outs[n].cpu().numpy(), M, S) <= FP32_TOL, n
+    # a part of the store (blco_mttkrp_range reads it in host memory too)
+    b = blco.blco_partition(spec.nnz, 3)
+    cs = c[t.perm()]
+    vs = t.values().cpu().numpy().astype(np.float64)
+    out = torch.empty((spec.dims[0], spec.rank), device="cuda")
+    blco.blco_mttkrp_range(t.handle, 0, int(b[1]), int(b[2]), A, blco.BLCO_F32, spec.rank, out)
+    M, S = oracle.mttkrp(cs[b[1]:b[2]], vs[b[1]:b[2]], spec.dims, Af, 0)
+    assert oracle.max_rel_err(out.cpu().numpy(), M, S) <= FP32_TOL
+    # CP model at the nonzeros (store order) and its adjoint with g in place of x
+    xhat = t.cp_fwd(A).cpu().numpy()
+    ref, scale = _cp_ref(t, coords, A)
+    assert float(np.max(np.abs(xhat - ref) / scale)) <= CP_TOL
+    g = torch.from_numpy(np.random.default_rng(3).standard_normal(spec.nnz).astype(np.float32)).cuda()
+    gb = t.cp_bwd(1, g, A)
+    M, S = oracle.mttkrp(cs, g.cpu().numpy().astype(np.float64), spec.dims, Af, 1)
+    assert oracle.max_rel_err(gb.cpu().numpy(), M, S) <= FP32_TOL
 
 
 @pytest.mark.parametrize("streamed", [False, True])

@@ -141,6 +141,41 @@ def test_roundtrip_exhaustive(orc, dims, line):
     assert np.all(np.diff(st.bstart) <= 7) and np.all(np.diff(st.bstart) > 0)
 
 
+@pytest.mark.parametrize("dims,line", [((0xFFFFFFFF,) * 4, 64), ((0xFFFFFFFF, (1 << 31) + 1, 3, 1), 64),
+                                       ((0xFFFFFFFF, 0xFFFFFFFF), 1)])
+def test_roundtrip_at_maximum_mode_lengths(orc, dims, line):
+    """Modes of the largest length the coordinates allow (2^32 - 1, 32 bits
+    each, up to 128 index bits): the ALTO order equals the recursive
+    bisection, and block high bits plus in-block fields give back every
+    coordinate, including the first and last index of each mode."""
+    rng = np.random.default_rng(11)
+    n = 300
+    coords = np.stack([rng.integers(0, d, n, dtype=np.uint64) for d in dims], 1).astype(np.int64)
+    coords[0] = 0
+    coords[1] = [d - 1 for d in dims]
+    coords = np.unique(coords, axis=0)
+    rng.shuffle(coords)
+    keys = orc.alto_keys_int(coords, dims)
+    by_key = [tuple(c) for _, c in sorted(zip(keys, coords.tolist()))]
+    by_cmp = sorted([tuple(c) for c in coords.tolist()], key=functools.cmp_to_key(_alto_cmp_recursive(dims)))
+    assert by_key == by_cmp
+    st = orc.build_store(coords.astype(np.uint32), np.ones(len(coords), np.float32), dims, line_bits=line,
+                         max_nnz=1 << 27)
+    bits = [_bits(d) for d in dims]
+    _, table = orc.alto_layout(dims)
+    kb = [0] * len(dims)
+    for m, _ in table[line:]:
+        kb[m] += 1
+    blk = np.searchsorted(st.bstart, np.arange(len(coords)), side="right") - 1
+    off = 0
+    for k, b in enumerate(bits):
+        w = b - kb[k]
+        field = (st.keys.astype(object) >> off) & ((1 << w) - 1)
+        got = (st.bhigh[blk, k].astype(object) << w) + np.array(field, dtype=object)
+        assert [int(x) for x in got] == coords[st.perm, k].tolist()
+        off += w
+
+
 def test_split_rule(orc):
     # one run of 10 entries (no block bits) with a cap of 4 -> pieces 4, 4, 2
     coords = np.array([[i] for i in range(10)])
