@@ -91,17 +91,20 @@ def test_empty_and_single():
 def test_empty_and_single_five_modes_one_pass(R):
     """The one-pass all-mode kernel on an empty 5-mode store (outputs zeroed,
     no launch) and on a single nonzero (every mode's row is the product of
-    the other four rows, every other row zero), also with a streamed store."""
+    the other four rows, every other row zero), also with a streamed store
+    and with one read in host memory."""
     dims = (5, 6, 7, 3, 1 << 20)
     A = [torch.randn(d, R, device="cuda") for d in dims]
-    t = blco.Tensor.build(torch.zeros((0, 5), dtype=torch.int32, device="cuda"), torch.zeros(0, device="cuda"), dims)
-    outs = [torch.full((d, R), 7.0, device="cuda") for d in dims]
-    t.mttkrp_all(A, outs=outs)
-    torch.cuda.synchronize()
-    assert all(torch.count_nonzero(o) == 0 for o in outs)
+    for kw in ({}, dict(force_stream=True, host_reads=True)):
+        t = blco.Tensor.build(torch.zeros((0, 5), dtype=torch.int32, device="cuda"), torch.zeros(0, device="cuda"),
+                              dims, **kw)
+        outs = [torch.full((d, R), 7.0, device="cuda") for d in dims]
+        t.mttkrp_all(A, outs=outs)
+        torch.cuda.synchronize()
+        assert all(torch.count_nonzero(o) == 0 for o in outs)
     c = torch.tensor([[4, 5, 6, 2, (1 << 20) - 1]], dtype=torch.int32, device="cuda")
     v = torch.tensor([-1.5], device="cuda")
-    for kw in ({}, dict(force_stream=True)):
+    for kw in ({}, dict(force_stream=True), dict(force_stream=True, host_reads=True)):
         t1 = blco.Tensor.build(c, v, dims, **kw)
         outs = t1.mttkrp_all(A)
         torch.cuda.synchronize()
