@@ -222,6 +222,14 @@ def noise(n: int, sigma: float, seed: int, device="cpu") -> torch.Tensor:
     return sigma * torch.randn(n, generator=gen, device=torch.device(device), dtype=torch.float32)
 
 
+def workload(name: str) -> TensorSpec:
+    """The workload of that name (e.g. "zipf1.1-4d-500M")."""
+    for spec in CONFIGS:
+        if spec.name == name:
+            return spec
+    raise KeyError(name)
+
+
 def small(index: int, nnz: int, dims: Sequence[int]) -> TensorSpec:
     """Configuration ``index``'s recipe at an oracle-sized shape."""
     return CONFIGS[index].scaled(nnz, dims)

@@ -87,7 +87,7 @@ def _store_samples(t, c, v, dims, line, cap, seed, n=200000):
 # --------------------------------------------------------------- 150M, 3 modes
 def test_zipf3d_150M_store_and_mttkrp():
     _tick("start")
-    spec = synth.CONFIGS[1]
+    spec = synth.workload("zipf1.2-3d-150M")
     coords = synth.coordinates(spec, device="cuda")
     vals = synth.values(spec, device="cuda")
     A = synth.factors(spec, device="cuda")
@@ -107,7 +107,7 @@ def test_zipf3d_150M_store_and_mttkrp():
 # --------------------------------------------------------------- 500M, 4 modes, BF16
 def test_zipf4d_500M_fp32_and_bf16():
     _tick("start")
-    spec = synth.CONFIGS[2]
+    spec = synth.workload("zipf1.1-4d-500M")
     coords = synth.coordinates(spec, device="cuda")
     vals = synth.values(spec, device="cuda")
     A = synth.factors(spec, device="cuda")
@@ -137,7 +137,7 @@ def test_zipf4d_500M_fp32_and_bf16():
 # --------------------------------------------------------------- 1B, 5 modes, streamed
 def test_zipf5d_1B_streamed_under_16GB():
     _tick("start")
-    spec = synth.CONFIGS[3]
+    spec = synth.workload("zipf1.2-5d-1B")
     coords = synth.coordinates(spec, device="cuda")
     vals = synth.values(spec, device="cuda")
     A = synth.factors(spec, device="cuda")
@@ -175,7 +175,7 @@ def _planted_values(coords, P, sigma, seed):
 
 def test_cp_planted_200M_fwd_bwd_and_als():
     _tick("start")
-    spec = synth.CONFIGS[4]
+    spec = synth.workload("cp-planted-3d-200M")
     coords = synth.coordinates(spec, device="cuda")
     P = synth.factors(spec, device="cuda", stream=5, dist="u01")          # planted rank-64 model
     vals = _planted_values(coords, P, 0.01, spec.seed + 99)

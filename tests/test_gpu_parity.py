@@ -173,7 +173,7 @@ def test_mttkrp_uniform_all_ranks(R):
 
 
 def test_mttkrp_uniform_100k_full():
-    spec = synth.CONFIGS[0]
+    spec = synth.workload("uniform-3d-100k")
     coords, vals, A = make(spec)
     t = blco.Tensor.build(coords, vals, spec.dims)
     check_mttkrp_all(t, coords, vals, A, spec.dims)
