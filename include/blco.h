@@ -170,10 +170,13 @@ blco_status blco_mttkrp(blco_handle h, int mode, const void *const *factors, blc
  * in the order the modes need them; each mode's kernel waits only for the
  * factors it gathers, and each host result is downloaded on a second copy
  * stream while the next mode runs. The call returns when the host results
- * are complete. On a streamed store each batch of blocks crosses the host
- * link once per call: while it sits in its queue's reservation the kernels
- * of every requested mode run on it (Section 4.2); the factors and all the
- * requested outputs stay on the device meanwhile.
+ * are complete. On a store streamed through the device queues each batch
+ * of blocks crosses the host link once per call: while it sits in its
+ * queue's reservation the kernels of every requested mode run on it
+ * (Section 4.2); the factors and all the requested outputs stay on the
+ * device meanwhile. On a store read in host memory (host_reads) the kernels
+ * load the store over the host link: once per call at 5 modes, once per
+ * requested mode otherwise.
  * A 5-mode store (every I_n <= 2^24, R = 16, 32 or 64) is computed in one
  * pass: each nonzero's five factor rows are gathered once and its product
  * goes to every requested output (Eq. 1 for all modes at once), one kernel
