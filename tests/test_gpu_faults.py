@@ -1,8 +1,9 @@
 """Failure handling, with every failure made on the host (blco_inject_fault):
 a device allocation that reports out-of-memory at each allocation point of a
-streamed build, and a batch copy of a streamed MTTKRP that fails mid-call.
-No GPU fault is raised; the library must report the error, release what it
-had, and leave the GPU and later handles working."""
+streamed build (through device queues, or read in host memory), and a batch
+copy of a streamed MTTKRP that fails mid-call. No GPU fault is raised; the
+library must report the error, release what it had, and leave the GPU and
+later handles working."""
 
 import numpy as np
 import pytest
@@ -34,14 +35,15 @@ def test_inject_fault_rejects_bad_arguments():
         assert ei.value.status == blco.BLCO_ERR_ARG
 
 
-def test_allocation_failure_at_every_point_of_a_streamed_build():
+@pytest.mark.parametrize("host_reads", [False, True])
+def test_allocation_failure_at_every_point_of_a_streamed_build(host_reads):
     coords, vals, A = make(_SPEC)
     torch.cuda.synchronize()
     failed = 0
     for k in range(1, 40):
         blco.blco_inject_fault(blco.BLCO_FAULT_ALLOC, k)
         try:
-            t = blco.Tensor.build(coords, vals, _SPEC.dims, **_BUILD)
+            t = blco.Tensor.build(coords, vals, _SPEC.dims, host_reads=host_reads, **_BUILD)
         except blco.BlcoError as e:
             assert e.status == blco.BLCO_ERR_OOM, str(e)
             assert "injected" in str(e) or "out of memory" in str(e).lower()
@@ -55,7 +57,7 @@ def test_allocation_failure_at_every_point_of_a_streamed_build():
         break
     else:
         pytest.fail("the build never got past its allocation points")
-    assert failed >= 3, "a streamed build allocates its store, queues and scratch"
+    assert failed >= 3, "a streamed build allocates its store, tables and scratch (and queues)"
 
 
 def test_copy_failure_mid_mttkrp_leaves_the_handle_usable():

@@ -440,14 +440,16 @@ def test_store_read_in_host_memory(order):
     assert oracle.max_rel_err(gb.cpu().numpy(), M, S) <= FP32_TOL
 
 
-@pytest.mark.parametrize("streamed", [False, True])
+@pytest.mark.parametrize("streamed", ["resident", "queues", "host"])
 def test_short_mode_output_copies(streamed):
     """R = 64 with 1024- and 600-row modes: those launches reduce into
     private output copies and sum the copies afterwards, also when the
-    batches of a streamed store run concurrently on several queues."""
+    batches of a streamed store run concurrently on several queues, and on
+    a store read in host memory."""
     spec = synth.small(4, 150_000, (1 << 16, 600, 1 << 10))
     coords, vals, A = make(spec)
-    kw = dict(force_stream=True, max_nnz_per_block=4000, n_queues=4) if streamed else {}
+    kw = {"queues": dict(force_stream=True, max_nnz_per_block=4000, n_queues=4),
+          "host": dict(force_stream=True, host_reads=True, max_nnz_per_block=4000)}.get(streamed, {})
     t = blco.Tensor.build(coords, vals, spec.dims, **kw)
     check_mttkrp_all(t, coords, vals, A, spec.dims)
     check_mttkrp_all(t, coords, vals, A, spec.dims, modes=[2, 1])  # again: copies reused
