@@ -736,7 +736,9 @@ def run_blco(args, ranks: Ranks):
     if name == CP_MODEL:
         head = measure_cp(blco, spec, args, ranks, dev, args.steps, args.warmup)
         head["clocks"] = None
-        metric = head["metric"]
+        head["value"] = head["f32"]["value"]
+        head["ms_per_step"] = head["f32"]["ms_per_step"]
+        metric = head.pop("metric")
         roof = None
     else:
         head = measure_mttkrp(blco, spec, args, ranks, dev, args.steps, args.warmup, headline=True,

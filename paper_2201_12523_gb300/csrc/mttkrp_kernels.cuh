@@ -467,10 +467,18 @@ __global__ void __launch_bounds__(kThreads, mttkrp_min_ctas<R, NG>()) k_mttkrp(c
         // range) to the row's accumulator where the run ends or the range
         // ends. Before the last step two lanes of the warp never flush the
         // same row in the same step (a run has one end), so warp-tier rows
-        // take a plain read-modify-write; at the last step the parts of runs
-        // that continue into the next range use atomics, ordered before the
-        // plain updates by __syncwarp.
+        // take a plain read-modify-write. At the last step the part of a run
+        // that continues into the next range meets another update of its row
+        // in that step only if the run also covers the next range up to its
+        // last position (that range then flushes the same row too); such
+        // parts use atomics, ordered before the plain updates by __syncwarp,
+        // and every other part is the only update of its row in the step.
         const unsigned ends = (heads >> 1) | 0x80000000u;  // bit s: a run ends at s
+        // the next range [(g+1)*G, (g+2)*G) has no run end before its last
+        // position (only used where a run continues past this range, so g+1
+        // is a range of the tile)
+        const bool next_unbroken =
+            g + 1 < 32 / G && ((ends >> (((g + 1) * STEPS) & 31)) & ((1u << (STEPS - 1)) - 1u)) == 0u;
         RunSum<COMP> acc[H];
 #pragma unroll
         for (int h = 0; h < H; ++h) acc[h].clear();
@@ -518,8 +526,9 @@ __global__ void __launch_bounds__(kThreads, mttkrp_min_ctas<R, NG>()) k_mttkrp(c
                     const uint32_t row = rsw.x;
                     const int sl = (int)rsw.y;
                     const bool warp_tier = sl >= 0;
-                    // continuation parts at the last step: atomics first
-                    const bool cont = last && !run_end && warp_tier;
+                    // continuation parts that meet another update at the
+                    // last step: atomics first
+                    const bool cont = last && !run_end && warp_tier && next_unbroken;
                     if (!warp_tier) {
                         float sv[VEC];
 #pragma unroll
