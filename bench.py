@@ -63,8 +63,8 @@ FP32_TOL, BF16_TOL = 1e-5, 1e-2
 # (profiles/), valid only for the kernel source it was taken from (sha256 of
 # the kernel header and its float32 translation unit): workload -> record.
 TRAFFIC_RECORDS = {
-    "zipf1.1-4d-500M": {"src_sha256": "018f32bfb77f4f82e8a396ed779b77d8b1807173beb832e3e2ffb5035b6276a4",
-                        "bytes_per_launch": 7.210e9},  # mean of modes 0-3, R = 32, float32 factors
+    "zipf1.1-4d-500M": {"src_sha256": "e6765c8922a7d71eafc404c1d1ce06398280425ae954f857e53e8aeec58b933b",
+                        "bytes_per_launch": 7.223e9},  # mean of modes 0-3, R = 32, float32 factors
     "zipf1.2-5d-1B": {"src_sha256": "c16df474c0ced002e24fc1c056d4e7cee614803c50b329a74341cd539b008162",
                       "bytes_per_launch": 28.785e9},  # one-pass all-mode launch, resident store, R = 16
 }
