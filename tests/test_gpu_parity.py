@@ -547,18 +547,22 @@ def test_partitioned_mttkrp_sums_to_the_full_result(parts):
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16, torch.float16])
 @pytest.mark.parametrize("R", [16, 32, 64])
-@pytest.mark.parametrize("which", ["5d", "5d-blocked", "5d-short"])
+@pytest.mark.parametrize("which", ["5d", "5d-blocked", "5d-short", "5d-host"])
 def test_all_mode_one_pass_matches_oracle(which, R, dtype):
     """blco_mttkrp_all on a 5-mode store gathers each nonzero's rows once for
     every mode (one kernel launch): every mode against the FP64 oracle, with
-    ragged tails, a blocked store with 2^24-row modes, modes short enough to
-    be held on chip whole, and a mode left out."""
+    ragged tails, a blocked store with 2^24-row modes (also read in host
+    memory), modes short enough to be held on chip whole, and a mode left
+    out."""
     if which == "5d":
         spec = synth.small(3, 60_013, (1 << 12, 1 << 10, 1 << 9, 1 << 6, 1 << 4))
         kw = {}
     elif which == "5d-blocked":
         spec = synth.small(3, 40_009, (1 << 24, 1 << 20, 1 << 16, 1 << 12, 1 << 8))
         kw = dict(max_nnz_per_block=5000)
+    elif which == "5d-host":
+        spec = synth.small(3, 40_009, (1 << 24, 1 << 20, 1 << 16, 1 << 12, 1 << 8))
+        kw = dict(max_nnz_per_block=5000, force_stream=True, host_reads=True)
     else:
         spec = synth.small(3, 20_011, (400, 9, 5, 3, 2))
         kw = {}
