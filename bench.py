@@ -83,6 +83,8 @@ def parse_args(argv=None):
     p.add_argument("--no-bf16", action="store_true")
     p.add_argument("--no-errors", action="store_true")
     p.add_argument("--no-extras", action="store_true")
+    p.add_argument("--f64", action="store_true",
+                   help="with --workload: also time the float64 path (values, factors, accumulation)")
     p.add_argument("--nnz", type=int, default=0, help="override the nonzero count (profiling captures only)")
     p.add_argument("--resident", action="store_true",
                    help="keep the store on the device for a workload that streams (profiling captures only)")
@@ -742,7 +744,7 @@ def run_blco(args, ranks: Ranks):
         roof = None
     else:
         head = measure_mttkrp(blco, spec, args, ranks, dev, args.steps, args.warmup, headline=True,
-                              sampler=sampler)
+                              sampler=sampler, with_f64=args.f64 and spec.name.split("@")[0] not in STREAMED)
         metric = "all-mode sparse MTTKRP throughput"
         roof = head.pop("roofline")
     line = {"metric": metric, "value": head.pop("value"), "unit": head.pop("unit", "nnz/s (all-mode)"),
